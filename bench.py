@@ -1,0 +1,365 @@
+"""Benchmark of the MMAS hot path on GB300 (one JSON line on stdout).
+
+A step is one MMAS iteration (Alg. 1's main loop body): construction by m ants
+with candidate lists, bitmask tabu and reservoir sampling, tour lengths,
+iteration/global best and limits, and the fused evaporation + deposit +
+choice_info pass.  The default workload is the n = 1000 uniform instance,
+m = 1000 ants, 32-nearest-neighbour candidate lists, rho = 0.02, alpha = 1,
+beta = 2, p_best = 0.01 (synthetic coordinates, seed 1001).
+
+  value        tours/s over K device-timed steps (CUDA events inside the
+               iteration graph, on the launching stream), inputs resident in
+               HBM, L2 flushed (256 MiB write) before every step;
+  e2e          the same metric through the public C ABI with host buffers:
+               mmas_create from host coordinates, then per step mmas_iterate
+               and mmas_best_tour into host memory;
+  roofline     the construction kernel (the dominant one): algorithmic bytes
+               per launch / its mean CUDA-event duration, against the measured
+               HBM copy bandwidth;
+  cpu_baseline the CPU oracle (test infrastructure) on the host cores, a
+               bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torch.distributed.run; every rank runs an independent
+colony (seed + rank) on its own GPU and rank 0 prints the line (weak scaling,
+no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (n, m, cl, instance kind, instance seed)
+    "uniform-n1000-cl32": dict(n=1000, m=1000, cl=32, kind="uniform", iseed=1001),
+    "uniform-n200-fullrow": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002),
+}
+PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
+METRIC = "candidate tours/sec (one MMAS iteration per step)"
+UNIT = "tours/s"
+FLUSH_BYTES = 256 << 20
+CONSTRUCT_SOURCES = ["paper_2003_11902_gb300/csrc/construct.cu",
+                     "paper_2003_11902_gb300/csrc/internal.cuh"]
+
+
+def _instance(w):
+    from paper_2003_11902_gb300 import instances as I
+    if w["kind"] == "uniform":
+        return I.uniform(w["n"], w["iseed"])
+    return I.clustered(w["n"], w["iseed"])
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per construction launch from the committed ncu summary, if the
+    kernel source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"construct_{workload}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("source_sha") != _source_sha(CONSTRUCT_SOURCES):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"mmas_clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={device_index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(w, xy, budget_s=12.0):
+    """The oracle as it stands, all host cores, whole iterations until budget_s."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, **PARAMS)
+    it, t0 = 0, time.perf_counter()
+    while True:
+        col.iterate(1, threads=cores)
+        it += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or it >= 200:
+            break
+    return {"value": w["m"] * it / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{it} whole iterations (all {w['m']} ants + pheromone update) of the "
+                      f"same workload, OpenMP over ants on {cores} threads, {el:.1f} s"}
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle times the same workload on the host cores."""
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    xy = _instance(w)
+    cores = os.cpu_count() or 1
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, **PARAMS)
+    t0 = time.perf_counter()
+    col.iterate(1, threads=cores)
+    t_iter = time.perf_counter() - t0
+    budget = 150.0
+    full = (args.steps + args.warmup) * t_iter <= budget
+    if full:
+        for _ in range(max(0, args.warmup - 1)):
+            col.iterate(1, threads=cores)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            col.iterate(1, threads=cores)
+            times.append(time.perf_counter() - t0)
+        tours = w["m"] * args.steps
+        sample = f"whole iterations ({w['m']} ants + pheromone update), {cores} threads"
+    else:
+        # bounded sample: each step constructs S ants of the current iteration
+        import concurrent.futures as cf
+        s_ants = max(cores, int(w["m"] * budget / ((args.steps + args.warmup) * t_iter)))
+        s_ants = min(s_ants, w["m"])
+        it = col.iteration
+        ants = np.linspace(0, w["m"] - 1, s_ants).astype(int)
+        times = []
+        with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+            for step in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                list(ex.map(lambda k: col.construct(it, int(k)), ants))
+                if step >= args.warmup:
+                    times.append(time.perf_counter() - t0)
+        tours = s_ants * args.steps
+        sample = (f"{s_ants} of {w['m']} ants constructed per step (construction only), "
+                  f"{cores} threads")
+    total = sum(times)
+    value = tours / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **_cfg(w)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cfg(w):
+    return {"n": w["n"], "m": w["m"], "cl": w["cl"], "instance": f"{w['kind']} seed {w['iseed']}",
+            **PARAMS}
+
+
+def algorithmic_construct_bytes(w):
+    """Bytes a construction launch must move: per step, cl candidate ids (2 B)
+    and reciprocal weights (4 B) -- or, without candidate lists, the n_unvisited
+    reciprocal weights (4 B each) -- plus the 4-byte tour entry per step."""
+    n, m, cl = w["n"], w["m"], w["cl"]
+    if cl > 0:
+        per_ant = (n - 1) * cl * 6 + 4 * n
+    else:
+        per_ant = 4 * (n * (n - 1) // 2) + 4 * n
+    return m * per_ant
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_11902_gb300 import Colony, _build, mmas
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+    _build.build()
+    xy = _instance(w)
+    seed = 1 + rank
+    stream = torch.cuda.current_stream()
+    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev,
+                 stream=stream.cuda_stream, **PARAMS)
+    col.enable_phase_timing(True)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        col.iterate(1)
+    col.synchronize()
+
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev) if rank == 0 else None
+    con, tot = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        col.iterate(1)
+        c, _, t = col.phase_times()  # synchronises the stream
+        con.append(c)
+        tot.append(t)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    if ws > 1:
+        dist.barrier()
+    total_ms = float(sum(tot))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = col.stats()
+    best_len, _ = col.best_tour()
+
+    # end to end through the C ABI with host buffers
+    e2e_total = 0.0
+    t0 = time.perf_counter()
+    col2 = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, stream=stream.cuda_stream,
+                  **PARAMS)
+    col2.synchronize()
+    e2e_total += time.perf_counter() - t0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        col2.iterate(1)
+        col2.best_tour()  # device -> host: scalar block + best tour
+        e2e_total += time.perf_counter() - t0
+    col2.close()
+    e2e_value = w["m"] * args.steps / e2e_total
+    if ws > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = ws * w["m"] * args.steps / float(t.item())
+
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        c_ms = statistics.mean(con)
+        algo = algorithmic_construct_bytes(w)
+        achieved = algo / (c_ms * 1e-3) / 1e9
+        traffic = _profiled_traffic(args.workload)
+        value = ws * w["m"] * args.steps / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, **_cfg(w), "parallelism": f"replicas{ws}",
+                       "l2": "flushed before every step (256 MiB write)",
+                       "timing": "CUDA events in the iteration graph, launching stream"},
+            "construct_ms": c_ms,
+            "construct_tours_per_s": w["m"] / (c_ms * 1e-3),
+            "roofline": {"kernel": "k_construct", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": algo},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["n"] / args.steps,
+                    "d2h_bytes_per_step": 4 * w["n"] + 64},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "best_len": best_len, "fallback_steps": st["fallback_steps"],
+            "wall_s": wall,
+            "paper_context": "V100, pr1002, cl=32, MMAS-WRS-BT: 0.93 ms construction "
+                             "(~1.08M tours/s), Table 6",
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, xy)
+        print(json.dumps(line), flush=True)
+    col.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform-n1000-cl32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

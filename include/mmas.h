@@ -1,0 +1,205 @@
+/*
+ * mmas.h -- C ABI of the GB300 MAX-MIN Ant System library (libmmas.so).
+ *
+ * The library runs the data-parallel hot path of the MAX-MIN Ant System for
+ * the symmetric TSP (Skinderowicz, "Implementing a GPU-based parallel MAX-MIN
+ * Ant System", FGCS 2020) on one NVIDIA GPU (sm_103a):
+ *   - solution construction by m ants (Alg. 1, inner loops), with candidate
+ *     lists (Sec. 4.3), a bitmask tabu (Sec. 4.1) and weighted reservoir
+ *     sampling of Eq. (1) (Alg. 4, logarithmic keys of Sec. 4.2.2);
+ *   - tour lengths, iteration best, global best and trail limits (Alg. 1);
+ *   - evaporation, deposit and clamping to [tau_min, tau_max] (Sec. 2.1),
+ *     fused with the refresh of choice_info (Sec. 2.1, Sec. 4.2.2).
+ *
+ * Conventions for every call:
+ *   - Pointers named in a call are HOST pointers unless stated otherwise; the
+ *     library copies what it needs and never keeps a caller pointer.
+ *   - Every call returns an mmas_status.  On failure the handle is left as it
+ *     was before the call and mmas_last_error() describes the failure.
+ *   - A handle is not thread-safe; use one handle per thread.
+ *   - mmas_iterate() and the other enqueueing calls are asynchronous on the
+ *     handle's stream; errors raised on the device (a timed-out wait, an
+ *     inconsistent state) surface at the next synchronising call.
+ *   - Results are deterministic: (instance, params, seed, iteration count)
+ *     fixes every tour, independent of launch shapes, because every random
+ *     draw is keyed by (seed, iteration, ant, step, slot) -- see mmas_params.
+ */
+#ifndef MMAS_H
+#define MMAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MMAS_OK = 0,
+    MMAS_EINVAL = 1,    /* a parameter or instance value is out of range     */
+    MMAS_ENOMEM = 2,    /* a device or host allocation failed                */
+    MMAS_ECUDA = 3,     /* a CUDA runtime call failed                        */
+    MMAS_EOVERFLOW = 4, /* n * max(d) does not fit a 32-bit tour length      */
+    MMAS_ETIMEOUT = 5,  /* a bounded device-side wait expired                */
+    MMAS_ESTATE = 6     /* the call does not fit the handle's state          */
+} mmas_status;
+
+/* A symmetric TSP instance on n cities (Sec. 2.1).  Exactly one of xy and
+ * dist is non-NULL.
+ *   xy   : host, n x 2 int32 coordinates (row-major).  Distances are the
+ *          TSPLIB rounded Euclidean nint(sqrt(dx^2 + dy^2)), computed exactly
+ *          in integers.  |x|, |y| < 2^30.
+ *   dist : host, n x n int32 distances, row-major, symmetric, >= 0, zero
+ *          diagonal.
+ * 3 <= n <= 65535 (node ids fit 16 bits, as in the paper's Table 1). */
+typedef struct {
+    int32_t n;
+    const int32_t *xy;
+    const int32_t *dist;
+} mmas_instance;
+
+/* Parameters.  mmas_default_params() fills the defaults shown.
+ *   m        ants per iteration, 1 <= m <= 1048576                 (n)
+ *   alpha    pheromone exponent of Eq. (1), >= 0                   (1)
+ *   beta     heuristic exponent of Eq. (1), >= 0                   (2)
+ *   rho      evaporation RATE: tau <- max((1 - rho) tau, tau_min), 0 < rho < 1.
+ *            The paper's rho is the persistence (its rho = 0.5 is rho = 0.5
+ *            here, its rho = 0.9 is rho = 0.1 here).                (0.02)
+ *   p_best   the Stuetzle-Hoos parameter fixing tau_min/tau_max, 0 < p_best < 1
+ *                                                                   (0.01)
+ *   cl       candidate-list length: 0 samples the whole row (Eq. (1) over all
+ *            unvisited nodes); 1..32 samples the cl nearest nodes (Sec. 4.3),
+ *            cl < n                                                (32)
+ *   seed     key of the counter-based generator (Philox4x32-10)    (1)
+ *   deposit  0: deposit on the iteration best, 1: on the global best (0)
+ *   fallback when every candidate of the current node is visited:
+ *            0: take the unvisited node of largest choice_info (ties -> lower id);
+ *            1: reservoir-sample all unvisited nodes                (0)
+ *   device   CUDA device ordinal                                   (0)
+ *   stream   cudaStream_t to enqueue on, or NULL for a private stream (NULL)
+ *
+ * Random draws: start node of ant k in iteration it = word 0 of
+ * Philox(ctr = (0xFFFFFFFF, 0, k, it)); candidate slot s at step t = word
+ * (t mod 4) of Philox(ctr = (s, t/4, k, it)); whole-row node v at step t =
+ * word (v mod 4) of Philox(ctr = (2^31 | v/4, t, k, it)); key = (seed_lo,
+ * seed_hi).  A word x maps to r = ((x >> 9) + 1/2) 2^-23 in (0,1). */
+typedef struct {
+    int32_t m;
+    float alpha;
+    float beta;
+    float rho;
+    float p_best;
+    int32_t cl;
+    uint64_t seed;
+    int32_t deposit;
+    int32_t fallback;
+    int32_t device;
+    void *stream;
+} mmas_params;
+
+typedef struct mmas_handle mmas_handle;
+
+/* Counters and launch facts of a handle (filled by mmas_stats). */
+typedef struct {
+    int64_t iterations;        /* completed iterations (the next iteration's index)  */
+    int64_t fallback_steps;    /* candidate-list fallbacks since create              */
+    int64_t nn_len;            /* nearest-neighbour tour length (initial limits)     */
+    int32_t best_len;          /* global best length, -1 before the first iteration  */
+    int32_t iter_best_len;     /* last iteration best, -1 before the first iteration */
+    float tau_min, tau_max;    /* current trail limits                               */
+    int32_t construct_grid;    /* CTAs of the construction kernel                    */
+    int32_t construct_block;   /* threads per CTA (one warp per ant)                 */
+    int32_t construct_staged;  /* 1 if the choice table is staged in shared memory   */
+    int32_t construct_smem;    /* dynamic shared memory per CTA, bytes               */
+    int32_t row_pitch;         /* elements per row of the n x n device matrices      */
+} mmas_stats_t;
+
+/* Fill *p with the defaults listed at mmas_params (m = 0 means "m = n"). */
+void mmas_default_params(mmas_params *p);
+
+/* Build a colony (Alg. 1 before the main loop, Sec. 2.1, Sec. 4.3): copy the
+ * instance to the device, compute distances, eta^beta = d^-beta (d clamped to
+ * >= 1), candidate lists ordered by (distance, id), the nearest-neighbour tour
+ * from node 0, tau_max = 1/(rho C_nn), tau_min = tau_max (1 - p)/((n/2 - 1) p)
+ * with p = p_best^(1/n), tau <- tau_max and choice_info.  Returns the handle
+ * in *out (NULL on failure).  Errors: EINVAL (bad value; message says which),
+ * EOVERFLOW (n * max d >= 2^31), ENOMEM, ECUDA.  Synchronises the stream. */
+mmas_status mmas_create(const mmas_instance *inst, const mmas_params *p, mmas_handle **out);
+
+/* Enqueue k >= 0 iterations of Alg. 1's main loop (construction, tour
+ * lengths, iteration best, global best and limits, evaporation, deposit,
+ * choice_info refresh), replayed from one CUDA graph per iteration.  No host
+ * synchronisation.  Errors: EINVAL (k < 0), ESTATE, ECUDA. */
+mmas_status mmas_iterate(mmas_handle *h, int32_t k);
+
+/* Synchronise, then copy the global-best tour (n ids) to tour_out (may be
+ * NULL) and its length to *len_out (may be NULL).  Errors: ESTATE before the
+ * first iteration, ETIMEOUT / ESTATE if a device-side check failed. */
+mmas_status mmas_best_tour(mmas_handle *h, int32_t *tour_out, int32_t *len_out);
+
+/* Free every resource of the handle (NULL is allowed). */
+void mmas_destroy(mmas_handle *h);
+
+/* Message of the last failed call on h, or of the calling thread's last
+ * failed mmas_create when h is NULL.  Never NULL; "" when nothing failed. */
+const char *mmas_last_error(const mmas_handle *h);
+
+/* ---- lower-level steps and state access (tests, benchmarks, resume) ---- */
+
+/* Enqueue construction only (Alg. 1 inner loops and the tour lengths) for the
+ * current iteration index, leaving pheromone, limits and the index as they
+ * are.  The tours are readable with mmas_get_tours. */
+mmas_status mmas_construct(mmas_handle *h);
+
+/* Enqueue the rest of one iteration with a caller-given tour (host, n ids, a
+ * permutation) of length len standing in for the iteration best: global best
+ * and limits (Alg. 1), evaporation, deposit, choice_info.  The iteration index
+ * is not advanced.  Errors: EINVAL (not a permutation, len <= 0). */
+mmas_status mmas_update(mmas_handle *h, const int32_t *tour, int32_t len);
+
+/* Synchronise and copy the last constructed tours (m x n, row-major) and
+ * their lengths (m).  Either pointer may be NULL. */
+mmas_status mmas_get_tours(mmas_handle *h, int32_t *tours, int32_t *lens);
+
+/* Synchronise and copy the pheromone matrix (n x n, row-major) and the
+ * current limits.  Any pointer may be NULL. */
+mmas_status mmas_get_pheromone(mmas_handle *h, float *tau, float *tau_min, float *tau_max);
+
+/* Replace the pheromone matrix (n x n, row-major, finite, > 0) and the limits
+ * (0 < tau_min <= tau_max), then refresh choice_info.  Enqueued. */
+mmas_status mmas_set_pheromone(mmas_handle *h, const float *tau, float tau_min, float tau_max);
+
+/* Synchronise and copy the set-up results: distances (n x n), eta^beta
+ * (n x n), candidate lists (n x cl) and the nearest-neighbour length.  Any
+ * pointer may be NULL. */
+mmas_status mmas_get_setup(mmas_handle *h, int32_t *dist, float *eta_beta, int32_t *cand,
+                           int64_t *nn_len);
+
+/* Set the iteration index used by the random draws of the next construction
+ * (for resuming a run, and for repeated draws under a fixed pheromone). */
+mmas_status mmas_set_iteration(mmas_handle *h, int32_t it);
+
+/* Synchronise and fill *out. */
+mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out);
+
+/* Block until all work enqueued by the handle has finished; report device-side
+ * errors (ETIMEOUT, ESTATE) raised since the last check. */
+mmas_status mmas_synchronize(mmas_handle *h);
+
+/* Phase timing (a measurement aid; the paper times its kernels with CUDA
+ * timers, Sec. 5).  enable != 0 re-records the iteration graph with CUDA
+ * event-record nodes before construction, after construction and after the
+ * pheromone pass; enable == 0 records it without them. */
+mmas_status mmas_enable_phase_timing(mmas_handle *h, int32_t enable);
+
+/* Synchronise and report the phase durations of the most recent iteration run
+ * by mmas_iterate with phase timing enabled, in milliseconds: construction
+ * (incl. tour lengths), the rest (best, limits, pheromone pass), and the whole
+ * iteration.  Any pointer may be NULL.  ESTATE if timing is not enabled or no
+ * timed iteration has run. */
+mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms, float *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMAS_H */

@@ -1,0 +1,235 @@
+// Internal declarations shared by the translation units of libmmas.so.
+// Device helpers, the device-resident scalar block, launch-argument structs and
+// the host-side launchers.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mmas {
+
+// ---------------------------------------------------------------------------
+// Error bits raised on the device; the host reads them at synchronising calls.
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    ERR_STAGE_TIMEOUT = 1u,   // a shared-memory staging wait gave up
+    ERR_NO_UNVISITED = 2u,    // a selection found no unvisited node (inconsistent tabu)
+};
+
+// Device-resident scalars of one colony.  Kernels read and write them, so a
+// captured CUDA graph replays whole iterations without host round trips.
+struct Scalars {
+    int32_t iter;          // index of the next iteration (keys the random draws)
+    int32_t gb_len;        // global best length, INT32_MAX before the first iteration
+    int32_t ib_len;        // last iteration best length (-1 before the first)
+    int32_t ib_ant;        // last iteration best ant
+    float tmin, tmax;      // trail limits
+    float delta;           // deposit amount of the pending update (float 1/C)
+    int32_t dep_len;       // length of the tour being deposited
+    uint32_t err;          // ERR_* bits
+    int32_t pad0;
+    unsigned long long fallback_steps;  // cumulative candidate-list fallbacks
+    long long nn_len;      // nearest-neighbour tour length
+    long long iterations;  // completed iterations
+};
+
+// ---------------------------------------------------------------------------
+// Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// Ten rounds; each multiplies words 0 and 2 by the round multipliers, mixes
+// the high halves with words 1 and 3 and the key, and bumps the key by the
+// Weyl increments.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// r = ((x >> 9) + 1/2) * 2^-23, exactly representable, in (0, 1).
+__device__ __forceinline__ float unit_open(uint32_t x)
+{
+    return __fmul_rn(__fadd_rn((float)(x >> 9), 0.5f), 1.1920928955078125e-7f);
+}
+
+// Order-preserving map of a float to uint32 (larger float -> larger code).
+// Codes are >= 1 for every non-NaN float, so 0 marks "no candidate".
+__device__ __forceinline__ uint32_t ord_key(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// TSPLIB rounded Euclidean distance nint(sqrt(s)), exact: q = floor(sqrt(s))
+// from a double square root corrected by integer comparisons, then
+// nint = q + [s > q^2 + q].  |coords| < 2^30 keeps s below 2^63.
+__device__ __forceinline__ int32_t euc2d_exact(int2 a, int2 b)
+{
+    const long long dx = (long long)a.x - b.x, dy = (long long)a.y - b.y;
+    const unsigned long long s = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
+    unsigned long long q = (unsigned long long)sqrt((double)s);
+    while (q * q > s) --q;
+    while ((q + 1) * (q + 1) <= s) ++q;
+    return (int32_t)(q + (s > q * q + q ? 1ull : 0ull));
+}
+
+// Trail limits (after Stuetzle and Hoos, as Sec. 5 states): tau_max = 1/(rho C),
+// tau_min = tau_max (1 - p)/((n/2 - 1) p), capped at tau_max; double, stored float.
+__device__ __forceinline__ void trail_limits(int32_t n, double rho, double p_root, long long cost, float *tmax,
+                             float *tmin)
+{
+    const double tx = __ddiv_rn(1.0, __dmul_rn(rho, (double)cost));
+    const double avg = __ddiv_rn((double)n, 2.0);
+    double tn = __ddiv_rn(__dmul_rn(tx, __dsub_rn(1.0, p_root)),
+                          __dmul_rn(__dsub_rn(avg, 1.0), p_root));
+    if (tn > tx) tn = tx;
+    *tmax = (float)tx;
+    *tmin = (float)tn;
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier + bulk asynchronous copy (TMA engine, non-tensor form) helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global to
+// this CTA's shared memory; completion is signalled on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar` for at most `limit_ns`; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Launch arguments
+// ---------------------------------------------------------------------------
+struct ConstructArgs {
+    int32_t n, m, cl, ld, fallback;
+    uint32_t key0, key1;
+    const int32_t *iter;       // device iteration index
+    const uint16_t *cand16;    // [n][cl] candidate ids
+    const float *cwinv;        // [n][cl] 1 / choice_info of each candidate
+    const float *wmat;         // [n][ld] choice_info (cl > 0) or 1/choice_info (cl == 0)
+    const int2 *xy;            // [n] coordinates, or nullptr (then dist is used)
+    const int32_t *dist;       // [n][ld]
+    int32_t *tours;            // [m][ld]
+    int32_t *lens;             // [m]
+    Scalars *sc;
+    uint32_t stage_w_bytes;    // bytes of the staged weight table (16-byte multiple)
+    uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
+};
+
+struct ConstructPlan {
+    int staged;     // stage the weight (and id) tables in shared memory
+    int regmask;    // tabu bitmask held in registers (n <= 1024)
+    int warps;      // warps (= ants in flight) per CTA
+    int grid;
+    size_t smem;    // dynamic shared memory bytes
+};
+
+struct BestArgs {
+    int32_t n, m, ld, deposit, advance;
+    double rho;        // evaporation rate as double
+    double p_root;     // p_best^(1/n)
+    const int32_t *lens;
+    const int32_t *tours;  // [m][ld]
+    int32_t *gb_tour;      // [n]
+    int2 *nbr;             // [n]: successor and predecessor in the deposited tour
+    Scalars *sc;
+};
+
+struct UpdateArgs {
+    int32_t n, ld, cl, fullrow, evaporate;
+    float persist;     // float(1 - rho)
+    float alpha;
+    const float *eb;   // [n][ld]
+    float *tau;        // [n][ld]
+    float *wmat;       // [n][ld]
+    const int32_t *cand32;  // [n][cl]
+    float *cwinv;      // [n][cl]
+    const int2 *nbr;   // [n] or nullptr (no deposit)
+    Scalars *sc;
+};
+
+// ---------------------------------------------------------------------------
+// Host launchers (return the launch's cudaError_t)
+// ---------------------------------------------------------------------------
+cudaError_t launch_distances(const int2 *xy, int32_t n, int32_t ld, int32_t *d, int *maxd,
+                             cudaStream_t s);
+cudaError_t launch_max_dist(const int32_t *d, int32_t n, int32_t ld, int *maxd, cudaStream_t s);
+cudaError_t launch_eta_beta(const int32_t *d, int32_t n, int32_t ld, double beta, float *eb,
+                            cudaStream_t s);
+cudaError_t launch_candidates(const int32_t *d, int32_t n, int32_t ld, int32_t cl,
+                              int32_t *cand32, uint16_t *cand16, cudaStream_t s);
+cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour,
+                           Scalars *sc, cudaStream_t s);
+cudaError_t launch_init_colony(int32_t n, int32_t ld, double rho, double p_root, float *tau,
+                               Scalars *sc, cudaStream_t s);
+
+cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
+                           ConstructPlan *plan);
+cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s);
+
+cudaError_t launch_best(const BestArgs &a, cudaStream_t s);
+cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s);
+
+}  // namespace mmas

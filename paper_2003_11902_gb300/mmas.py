@@ -1,0 +1,306 @@
+"""Python binding of libmmas.so (declared in include/mmas.h).
+
+Argument marshalling only: every step of the MMAS hot path runs in the CUDA
+library.  The functions keep the C ABI's names (``mmas_create``,
+``mmas_iterate``, ...); ``Colony`` wraps a handle for convenience.  PyTorch, when
+importable, supplies the CUDA stream (its current stream) and nothing else.
+
+If the library has not been built, every call raises ``RuntimeError``; there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmmas.so")
+
+MMAS_OK, MMAS_EINVAL, MMAS_ENOMEM, MMAS_ECUDA, MMAS_EOVERFLOW, MMAS_ETIMEOUT, MMAS_ESTATE = range(7)
+STATUS_NAMES = {0: "MMAS_OK", 1: "MMAS_EINVAL", 2: "MMAS_ENOMEM", 3: "MMAS_ECUDA",
+                4: "MMAS_EOVERFLOW", 5: "MMAS_ETIMEOUT", 6: "MMAS_ESTATE"}
+
+# Every symbol include/mmas.h declares.
+EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour",
+           "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
+           "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
+           "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
+           "mmas_phase_times"]
+
+
+class mmas_instance(C.Structure):
+    _fields_ = [("n", C.c_int32), ("xy", C.POINTER(C.c_int32)), ("dist", C.POINTER(C.c_int32))]
+
+
+class mmas_params(C.Structure):
+    _fields_ = [("m", C.c_int32), ("alpha", C.c_float), ("beta", C.c_float), ("rho", C.c_float),
+                ("p_best", C.c_float), ("cl", C.c_int32), ("seed", C.c_uint64),
+                ("deposit", C.c_int32), ("fallback", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class mmas_stats_t(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("fallback_steps", C.c_int64), ("nn_len", C.c_int64),
+                ("best_len", C.c_int32), ("iter_best_len", C.c_int32), ("tau_min", C.c_float),
+                ("tau_max", C.c_float), ("construct_grid", C.c_int32),
+                ("construct_block", C.c_int32), ("construct_staged", C.c_int32),
+                ("construct_smem", C.c_int32), ("row_pitch", C.c_int32)]
+
+
+class MMASError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmmas.so (once) and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first")
+        L = C.CDLL(path)
+        H = C.c_void_p
+        P = C.POINTER
+        i32, i64, f32 = C.c_int32, C.c_int64, C.c_float
+        sigs = {
+            "mmas_default_params": (None, [P(mmas_params)]),
+            "mmas_create": (C.c_int, [P(mmas_instance), P(mmas_params), P(H)]),
+            "mmas_iterate": (C.c_int, [H, i32]),
+            "mmas_best_tour": (C.c_int, [H, P(i32), P(i32)]),
+            "mmas_destroy": (None, [H]),
+            "mmas_last_error": (C.c_char_p, [H]),
+            "mmas_construct": (C.c_int, [H]),
+            "mmas_update": (C.c_int, [H, P(i32), i32]),
+            "mmas_get_tours": (C.c_int, [H, P(i32), P(i32)]),
+            "mmas_get_pheromone": (C.c_int, [H, P(f32), P(f32), P(f32)]),
+            "mmas_set_pheromone": (C.c_int, [H, P(f32), f32, f32]),
+            "mmas_get_setup": (C.c_int, [H, P(i32), P(f32), P(i32), P(i64)]),
+            "mmas_set_iteration": (C.c_int, [H, i32]),
+            "mmas_stats": (C.c_int, [H, P(mmas_stats_t)]),
+            "mmas_synchronize": (C.c_int, [H]),
+            "mmas_enable_phase_timing": (C.c_int, [H, i32]),
+            "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _i32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _f32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _check(h, status):
+    if status != MMAS_OK:
+        msg = load().mmas_last_error(h)
+        raise MMASError(status, msg.decode() if msg else "")
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------- C-named wrappers
+
+def mmas_default_params() -> mmas_params:
+    p = mmas_params()
+    load().mmas_default_params(C.byref(p))
+    return p
+
+
+def mmas_create(xy=None, dist=None, params: mmas_params | None = None):
+    """Create a colony; returns (handle, keep-alive tuple).  Raises MMASError."""
+    if (xy is None) == (dist is None):
+        raise ValueError("give exactly one of xy and dist")
+    p = params if params is not None else mmas_default_params()
+    inst = mmas_instance()
+    keep = []
+    if xy is not None:
+        a = np.ascontiguousarray(xy, dtype=np.int32)
+        inst.n, inst.xy = a.shape[0], _i32p(a)
+        keep.append(a)
+    else:
+        a = np.ascontiguousarray(dist, dtype=np.int32)
+        inst.n, inst.dist = a.shape[0], _i32p(a)
+        keep.append(a)
+    h = C.c_void_p()
+    st = load().mmas_create(C.byref(inst), C.byref(p), C.byref(h))
+    _check(None, st)
+    return h
+
+
+def mmas_iterate(h, k: int = 1):
+    _check(h, load().mmas_iterate(h, k))
+
+
+def mmas_best_tour(h, n: int):
+    tour = np.zeros(n, np.int32)
+    length = C.c_int32()
+    _check(h, load().mmas_best_tour(h, _i32p(tour), C.byref(length)))
+    return length.value, tour
+
+
+def mmas_destroy(h):
+    load().mmas_destroy(h)
+
+
+def mmas_last_error(h=None) -> str:
+    msg = load().mmas_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def mmas_construct(h):
+    _check(h, load().mmas_construct(h))
+
+
+def mmas_update(h, tour, length: int):
+    t = np.ascontiguousarray(tour, dtype=np.int32)
+    _check(h, load().mmas_update(h, _i32p(t), int(length)))
+
+
+def mmas_get_tours(h, m: int, n: int):
+    tours = np.zeros((m, n), np.int32)
+    lens = np.zeros(m, np.int32)
+    _check(h, load().mmas_get_tours(h, _i32p(tours), _i32p(lens)))
+    return tours, lens
+
+
+def mmas_get_pheromone(h, n: int):
+    tau = np.zeros((n, n), np.float32)
+    tmin, tmax = C.c_float(), C.c_float()
+    _check(h, load().mmas_get_pheromone(h, _f32p(tau), C.byref(tmin), C.byref(tmax)))
+    return tau, np.float32(tmin.value), np.float32(tmax.value)
+
+
+def mmas_set_pheromone(h, tau, tmin, tmax):
+    t = np.ascontiguousarray(tau, dtype=np.float32)
+    _check(h, load().mmas_set_pheromone(h, _f32p(t), float(tmin), float(tmax)))
+
+
+def mmas_get_setup(h, n: int, cl: int):
+    dist = np.zeros((n, n), np.int32)
+    eb = np.zeros((n, n), np.float32)
+    cand = np.zeros((n, max(cl, 1)), np.int32)
+    nn_len = C.c_int64()
+    _check(h, load().mmas_get_setup(h, _i32p(dist), _f32p(eb), _i32p(cand), C.byref(nn_len)))
+    return dist, eb, cand[:, :cl], nn_len.value
+
+
+def mmas_set_iteration(h, it: int):
+    _check(h, load().mmas_set_iteration(h, int(it)))
+
+
+def mmas_stats(h) -> dict:
+    s = mmas_stats_t()
+    _check(h, load().mmas_stats(h, C.byref(s)))
+    return {f: getattr(s, f) for f, _ in mmas_stats_t._fields_}
+
+
+def mmas_synchronize(h):
+    _check(h, load().mmas_synchronize(h))
+
+
+def mmas_enable_phase_timing(h, enable: bool = True):
+    _check(h, load().mmas_enable_phase_timing(h, 1 if enable else 0))
+
+
+def mmas_phase_times(h):
+    """(construct_ms, rest_ms, total_ms) of the last timed iteration."""
+    a, b, c = C.c_float(), C.c_float(), C.c_float()
+    _check(h, load().mmas_phase_times(h, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------- Colony
+
+class Colony:
+    """One MMAS colony on the GPU (a handle of libmmas.so)."""
+
+    def __init__(self, xy=None, dist=None, m=None, alpha=1.0, beta=2.0, rho=0.02, p_best=0.01,
+                 cl=32, seed=1, deposit=0, fallback=0, device=0, stream="torch"):
+        p = mmas_default_params()
+        n = (np.asarray(xy) if xy is not None else np.asarray(dist)).shape[0]
+        p.m = int(m) if m is not None else n
+        p.alpha, p.beta, p.rho, p.p_best = alpha, beta, rho, p_best
+        p.cl, p.seed, p.deposit, p.fallback, p.device = cl, int(seed), deposit, fallback, device
+        if stream == "torch":
+            stream = _torch_stream()
+        p.stream = stream
+        self.n, self.m, self.cl = n, p.m, cl
+        self._h = mmas_create(xy=xy, dist=dist, params=p)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            mmas_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def iterate(self, k: int = 1):
+        mmas_iterate(self._h, k)
+
+    def construct(self):
+        mmas_construct(self._h)
+
+    def update(self, tour, length):
+        mmas_update(self._h, tour, length)
+
+    def best_tour(self):
+        return mmas_best_tour(self._h, self.n)
+
+    def tours(self):
+        return mmas_get_tours(self._h, self.m, self.n)
+
+    def pheromone(self):
+        return mmas_get_pheromone(self._h, self.n)
+
+    def set_pheromone(self, tau, tmin, tmax):
+        mmas_set_pheromone(self._h, tau, tmin, tmax)
+
+    def setup(self):
+        d, eb, cand, nn_len = mmas_get_setup(self._h, self.n, self.cl)
+        return {"d": d, "eta_beta": eb, "cand": cand, "nn_len": nn_len}
+
+    def set_iteration(self, it: int):
+        mmas_set_iteration(self._h, it)
+
+    def stats(self) -> dict:
+        return mmas_stats(self._h)
+
+    def synchronize(self):
+        mmas_synchronize(self._h)
+
+    def enable_phase_timing(self, enable: bool = True):
+        mmas_enable_phase_timing(self._h, enable)
+
+    def phase_times(self):
+        return mmas_phase_times(self._h)

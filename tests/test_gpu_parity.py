@@ -1,0 +1,315 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integers (distances, candidate lists, nearest-neighbour length, tour lengths)
+must be bit-exact.  Pheromone must agree to 1e-5 relative.  Node picks driven by
+the same counters must agree except at near-ties (see tests/parity.py), whose
+rate is printed.  Inputs come from the seeded generators only.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_11902_gb300 import Colony, MMASError, instances as I, mmas
+from parity import check_ant, is_permutation
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _pair(xy=None, dist=None, **kw):
+    g = Colony(xy=xy, dist=dist, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("m", "cl", "alpha", "beta", "rho", "p_best",
+                                                 "seed", "deposit", "fallback")}
+    for k in ("alpha", "beta", "p_best"):
+        if k in okw:
+            okw[k] = float(np.float32(okw[k]))
+    if "p_best" not in okw:
+        okw["p_best"] = float(np.float32(0.01))
+    o = O.Colony(xy=xy, dist=dist, **okw)
+    return g, o
+
+
+def _ulps(a, b):
+    ai = a.view(np.int32).astype(np.int64)
+    bi = b.view(np.int32).astype(np.int64)
+    return np.abs(ai - bi)
+
+
+# ------------------------------------------------------------------ set-up
+
+@pytest.mark.parametrize("n,cl,src", [(3, 1, "xy"), (5, 2, "xy"), (33, 8, "xy"), (200, 0, "xy"),
+                                      (300, 12, "dist"), (1000, 32, "xy"), (1500, 16, "xy")])
+def test_setup_matches_oracle(n, cl, src):
+    xy = I.uniform(n, 100 + n)
+    kw = dict(m=8, cl=cl, rho=0.02, seed=1)
+    if src == "xy":
+        g, o = _pair(xy=xy, **kw)
+    else:
+        g, o = _pair(dist=O.distances(xy), **kw)
+    s, st = g.setup(), o.state()
+    assert np.array_equal(s["d"], st["d"])
+    assert np.array_equal(s["cand"], st["cand"])
+    assert s["nn_len"] == o.nn_len
+    assert _ulps(s["eta_beta"], st["eta_beta"]).max() <= 1
+    tau, tmin, tmax = g.pheromone()
+    assert (tmin, tmax) == tuple(o.limits())
+    assert np.array_equal(tau, st["tau"])
+    g.close()
+
+
+def test_setup_clustered_3800():
+    xy = I.clustered(3800, 3)
+    g, o = _pair(xy=xy, m=4, cl=16, seed=1)
+    s, st = g.setup(), o.state()
+    assert np.array_equal(s["d"], st["d"]) and np.array_equal(s["cand"], st["cand"])
+    assert s["nn_len"] == o.nn_len
+    g.close()
+
+
+# ------------------------------------------------------------------ construction
+
+CONSTRUCT_CASES = [
+    # n, m, cl, fallback, source             path exercised
+    (40, 40, 8, 0, "xy"),        # staged table, register tabu
+    (200, 200, 0, 0, "xy"),      # whole row, staged 1/choice matrix (the n = 200 workload)
+    (300, 64, 0, 0, "dist"),     # whole row, unstaged, lengths from the matrix
+    (700, 40, 0, 0, "xy"),       # whole row, unstaged, register tabu
+    (1100, 48, 32, 0, "xy"),     # candidate lists, staged, shared-memory tabu
+    (1200, 16, 0, 0, "xy"),      # whole row, shared-memory tabu
+    (2000, 40, 32, 0, "xy"),     # candidate lists, unstaged, shared-memory tabu
+    (60, 60, 3, 1, "xy"),        # short lists, reservoir fallback over the row
+    (60, 60, 1, 0, "xy"),        # cl = 1: greedy fallback on most steps
+    (3, 5, 0, 0, "xy"), (3, 5, 1, 0, "xy"), (3, 4, 2, 0, "dist"),  # smallest instances
+    (10, 1, 9, 0, "xy"),         # cl = n - 1, a single ant
+]
+
+
+@pytest.mark.parametrize("n,m,cl,fb,src", CONSTRUCT_CASES)
+def test_first_iteration_tours_match_oracle(n, m, cl, fb, src):
+    xy = I.uniform(n, 200 + n)
+    kw = dict(m=m, cl=cl, fallback=fb, rho=0.05, seed=11)
+    g, o = _pair(xy=xy, **kw) if src == "xy" else _pair(dist=O.distances(xy), **kw)
+    g.construct()
+    tours, lens = g.tours()
+    d = o.state()["d"]
+    kinds = []
+    for k in range(m):
+        assert is_permutation(tours[k], n)
+        assert lens[k] == O.tour_length(d, tours[k])
+        kinds.append(check_ant(o, 0, k, tours[k], lens[k]))
+    near = kinds.count("near_tie")
+    print(f"n={n} m={m} cl={cl}: {m - near} exact, {near} near-tie divergences")
+    assert near <= max(1, m // 50)
+    g.close()
+
+
+def test_lockstep_iterations_match_oracle():
+    """Whole-run parity: as long as every pick agrees, tours, lengths, limits,
+    best tour and pheromone agree after every iteration."""
+    n, m = 60, 60
+    xy = I.uniform(n, 77)
+    g, o = _pair(xy=xy, m=m, cl=10, rho=0.1, seed=5)
+    tracked = 0
+    for it in range(40):
+        g.iterate(1)
+        tours, lens = g.tours()
+        kinds = [check_ant(o, it, k, tours[k], lens[k]) for k in range(m)]
+        o.iterate(1)
+        if "near_tie" in kinds:
+            break
+        otours, olens, _ = o.tours()
+        assert np.array_equal(tours, otours) and np.array_equal(lens, olens)
+        tau, tmin, tmax = g.pheromone()
+        assert (tmin, tmax) == tuple(o.limits())
+        np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
+        blen, btour = g.best_tour()
+        olen, otour = o.best()
+        assert blen == olen and np.array_equal(btour, otour)
+        tracked += 1
+    print(f"tracked {tracked} iterations exactly")
+    assert tracked >= 10
+    st = g.stats()
+    assert st["iterations"] == tracked + (0 if tracked == 40 else 1)
+    g.close()
+
+
+# ------------------------------------------------------------------ pheromone update
+
+@pytest.mark.parametrize("n,cl,deposit,alpha", [(50, 8, 0, 1.0), (257, 0, 0, 1.0), (1000, 32, 0, 1.0),
+                                                (130, 16, 1, 1.0), (90, 8, 0, 0.75)])
+def test_update_matches_oracle(n, cl, deposit, alpha):
+    xy = I.uniform(n, 300 + n)
+    rho = 0.02
+    g, o = _pair(xy=xy, m=4, cl=cl, rho=rho, seed=2, deposit=deposit, alpha=alpha)
+    tmin0, tmax0 = np.float32(1e-5), np.float32(2e-4)
+    tau0 = I.random_pheromone(n, 9, float(tmin0), float(tmax0))
+    np.fill_diagonal(tau0, tmax0)
+    g.set_pheromone(tau0, tmin0, tmax0)
+    tour = I.random_permutation(n, 10)
+    length = int(O.tour_length(o.state()["d"], tour))
+    g.update(tour, length)
+    tau, tmin, tmax = g.pheromone()
+    want_tmax, want_tmin = O.limits(n, np.float32(rho), float(np.float32(0.01)), length)
+    assert (tmin, tmax) == (want_tmin, want_tmax)
+    want = O.evaporate(tau0, O.persist_factor(rho), want_tmin, want_tmax)
+    want = O.deposit(want, tour, np.float32(1.0 / length), want_tmax)
+    np.testing.assert_allclose(tau, want, rtol=1e-5, atol=0)
+    print(f"update n={n}: max |ulp| difference {int(_ulps(tau, want).max())}")
+    blen, btour = g.best_tour()
+    assert blen == length and np.array_equal(btour, tour)
+    g.close()
+
+
+def test_pheromone_invariants_and_closed_form_at_full_size():
+    """n = 1000, m = 1000, cl = 32: after each iteration tau_min <= tau <= tau_max,
+    tau symmetric; an edge off every deposited tour follows max(tau (1-rho)^t, tau_min)."""
+    n = 1000
+    xy = I.uniform(n, 1001)
+    g = Colony(xy=xy, m=1000, cl=32, rho=0.02, seed=1)
+    tau_prev, _, _ = g.pheromone()
+    seen = np.zeros((n, n), bool)
+    for it in range(6):
+        g.iterate(1)
+        tau, tmin, tmax = g.pheromone()
+        assert np.all(tau >= tmin) and np.all(tau <= tmax)
+        assert np.array_equal(tau, tau.T)
+        blen, btour = g.best_tour()
+        _, lens = g.tours()
+        ib = int(np.argmin(lens))
+        tours, _ = g.tours()
+        t = tours[ib]
+        seen[t, np.roll(t, -1)] = True
+        seen[np.roll(t, -1), t] = True
+        untouched = ~seen
+        np.fill_diagonal(untouched, False)
+        persist = O.persist_factor(0.02)
+        want = np.minimum(np.maximum(tau_prev * persist, tmin), tmax)
+        assert np.array_equal(tau[untouched], want[untouched])
+        tau_prev = tau
+    g.close()
+
+
+# ------------------------------------------------------------------ selection statistics
+
+@pytest.mark.parametrize("cl", [0, 4])
+def test_gpu_pick_frequencies_follow_eq1(cl):
+    from scipy import stats
+    n = 7
+    xy = I.uniform(n, 21, side=100)
+    g = Colony(xy=xy, m=2048, cl=cl, seed=77)
+    o = O.Colony(xy=xy, m=1, cl=cl, seed=77)
+    ch = o.state()["choice"].astype(np.float64)
+    cand = o.state()["cand"]
+    firsts = []
+    for it in range(24):
+        g.set_iteration(it)
+        g.construct()
+        tours, _ = g.tours()
+        firsts.append(tours[:, :3].copy())
+    f = np.concatenate(firsts)
+    for s in range(n):
+        allowed = [j for j in range(n) if j != s] if cl == 0 else list(cand[s])
+        picks = f[f[:, 0] == s, 1]
+        counts = np.array([(picks == j).sum() for j in allowed], float)
+        assert counts.sum() == len(picks)
+        p = ch[s, allowed] / ch[s, allowed].sum()
+        assert stats.chisquare(counts, p * counts.sum()).pvalue > 1e-4
+    # second step given (start, first)
+    for s in range(n):
+        for j1 in range(n):
+            picks = f[(f[:, 0] == s) & (f[:, 1] == j1), 2]
+            if len(picks) < 500:
+                continue
+            allowed = [j for j in (range(n) if cl == 0 else cand[j1]) if j not in (s, j1)]
+            if not allowed:
+                continue
+            counts = np.array([(picks == j).sum() for j in allowed], float)
+            assert counts.sum() == len(picks)
+            p = ch[j1, allowed] / ch[j1, allowed].sum()
+            assert stats.chisquare(counts, p * counts.sum()).pvalue > 1e-4
+    g.close()
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_full_size_n1000_cl32_sampled_parity():
+    """The n = 1000, m = 1000, cl = 32 workload in the launch configuration the
+    benchmark times: every tour valid with an exact length; a sample of ants
+    matches the oracle pick for pick."""
+    n = m = 1000
+    xy = I.uniform(n, 1001)
+    g = Colony(xy=xy, m=m, cl=32, rho=0.02, seed=1)
+    o = O.Colony(xy=xy, m=m, cl=32, rho=0.02, seed=1)
+    g.iterate(1)
+    tours, lens = g.tours()
+    d = o.state()["d"]
+    for k in range(m):
+        assert is_permutation(tours[k], n)
+        assert lens[k] == O.tour_length(d, tours[k])
+    kinds = [check_ant(o, 0, k, tours[k], lens[k]) for k in range(0, m, 40)]
+    print(f"n=1000 sampled ants: {kinds.count('exact')} exact, {kinds.count('near_tie')} near-tie")
+    st = g.stats()
+    assert st["construct_staged"] == 1 and st["iterations"] == 1
+    frac = st["fallback_steps"] / (m * (n - 1))
+    print(f"fallback fraction {frac:.4f}")
+    assert 0.0 < frac < 0.2
+    assert st["best_len"] == lens.min() and st["iter_best_len"] == lens.min()
+    g.close()
+
+
+def test_full_size_n200_full_row_all_ants():
+    n = m = 200
+    xy = I.uniform(n, 1002)
+    g, o = _pair(xy=xy, m=m, cl=0, rho=0.02, seed=1)
+    g.iterate(1)
+    tours, lens = g.tours()
+    kinds = [check_ant(o, 0, k, tours[k], lens[k]) for k in range(m)]
+    print(f"n=200 full row: {kinds.count('exact')} exact, {kinds.count('near_tie')} near-tie")
+    assert kinds.count("near_tie") <= 2
+    g.close()
+
+
+# ------------------------------------------------------------------ errors and determinism
+
+def test_errors_leave_the_handle_usable():
+    xy = I.uniform(30, 5)
+    g = Colony(xy=xy, m=10, cl=5)
+    with pytest.raises(MMASError) as e:
+        g.best_tour()
+    assert e.value.status == mmas.MMAS_ESTATE
+    bad = np.arange(30, dtype=np.int32)
+    bad[3] = 4
+    with pytest.raises(MMASError, match="permutation"):
+        g.update(bad, 100)
+    tau, tmin, tmax = g.pheromone()
+    with pytest.raises(MMASError, match="finite"):
+        g.set_pheromone(np.zeros_like(tau), tmin, tmax)
+    tau2, _, _ = g.pheromone()
+    assert np.array_equal(tau, tau2)
+    g.iterate(2)
+    length, tour = g.best_tour()
+    assert is_permutation(tour, 30) and length > 0
+    g.close()
+
+
+def test_same_seed_same_run_any_stream():
+    torch = pytest.importorskip("torch")
+    xy = I.uniform(150, 9)
+    a = Colony(xy=xy, m=100, cl=16, seed=4)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = Colony(xy=xy, m=100, cl=16, seed=4)
+        b.iterate(5)
+    a.iterate(5)
+    assert np.array_equal(a.tours()[0], b.tours()[0])
+    assert np.array_equal(a.pheromone()[0], b.pheromone()[0])
+    c = Colony(xy=xy, m=100, cl=16, seed=5)
+    c.iterate(5)
+    assert not np.array_equal(a.tours()[0], c.tours()[0])
+    for x in (a, b, c):
+        x.close()
