@@ -180,12 +180,12 @@ mmas_status capture_iteration(mmas_handle *h)
     cudaStream_t cs;
     CK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[0], cs);
+    if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[0], cs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_construct(h->cargs, h->cplan, cs);
-    if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[1], cs);
+    if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[1], cs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_best(h->bargs, cs);
     if (e == cudaSuccess) e = launch_update(h->uargs, h->num_sms, cs);
-    if (e == cudaSuccess && h->timing) e = cudaEventRecord(h->ev[2], cs);
+    if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[2], cs, cudaEventRecordExternal);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);

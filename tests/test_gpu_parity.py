@@ -313,3 +313,27 @@ def test_same_seed_same_run_any_stream():
     assert not np.array_equal(a.tours()[0], c.tours()[0])
     for x in (a, b, c):
         x.close()
+
+
+def test_phase_timing_is_a_pure_measurement():
+    xy = I.uniform(120, 13)
+    a = Colony(xy=xy, m=64, cl=16, seed=3)
+    b = Colony(xy=xy, m=64, cl=16, seed=3)
+    with pytest.raises(MMASError) as e:
+        a.phase_times()
+    assert e.value.status == mmas.MMAS_ESTATE
+    a.enable_phase_timing(True)
+    a.iterate(3)
+    b.iterate(3)
+    c, r, t = a.phase_times()
+    assert c > 0 and r > 0 and abs(t - (c + r)) < 1e-4
+    assert np.array_equal(a.tours()[0], b.tours()[0])
+    assert np.array_equal(a.pheromone()[0], b.pheromone()[0])
+    a.enable_phase_timing(False)
+    a.iterate(1)
+    b.iterate(1)
+    assert np.array_equal(a.tours()[0], b.tours()[0])
+    with pytest.raises(MMASError):
+        a.phase_times()
+    a.close()
+    b.close()
