@@ -7,12 +7,13 @@
 // (Sec. 4.1) and appends it to the tour.
 //
 //  - Candidate-list mode (cl in 1..32, Sec. 4.3): lane c scores candidate
-//    slot c.  The slot's uniform depends on (iteration, ant, step, slot) only,
-//    so one Philox call yields the draws of four consecutive steps and the
-//    log2 of each is taken off the step-to-step dependency chain.  When every
-//    candidate is visited, the fallback scans the unvisited nodes of the row.
+//    slot c.  A slot's uniform depends on (iteration, ant, step, slot) only, so
+//    one Philox call yields the draws of four consecutive steps, and the call
+//    for the next four steps (and its log2s) is spread over the current four
+//    steps, filling the latency of the step-to-step dependency chain.  When
+//    every candidate is visited, an out-of-line fallback scans the row.
 //  - Whole-row mode (cl = 0): lane l scores nodes 4c..4c+3 for c = l, l+32, ...,
-//    reading 16 bytes of 1/choice_info per chunk and one Philox call per chunk.
+//    reading 16 bytes of 1/choice_info per chunk, one Philox call per chunk.
 //
 // The table a step reads (n x cl ids + reciprocal weights, or the n x ld
 // reciprocal weight matrix) is copied into shared memory once per CTA with the
@@ -20,7 +21,8 @@
 // The tabu of an ant lives in registers (lane l holds nodes 32l..32l+31) when
 // n <= 1024, otherwise in the warp's slice of shared memory.
 // Tour entries are buffered one per lane and written as 128-byte rows every 32
-// steps; each lane then adds the length of its edge.
+// steps; each lane then adds the length of its edge (coordinates: computed
+// exactly in registers; explicit matrix: loaded one window ahead of its use).
 #include "internal.cuh"
 
 namespace mmas {
@@ -32,15 +34,6 @@ constexpr unsigned long long STAGE_LIMIT_NS = 2000000000ull;  // 2 s
 constexpr uint32_t BULK_CHUNK = 32768u;
 
 enum { CAND = 0, ROW = 1 };
-
-template <bool XY>
-__device__ __forceinline__ int32_t edge_len(const ConstructArgs &a, int u, int v)
-{
-    if constexpr (XY)
-        return euc2d_exact(__ldg(a.xy + u), __ldg(a.xy + v));
-    else
-        return __ldg(a.dist + (size_t)u * a.ld + v);
-}
 
 // Bitmask tabu (Sec. 4.1, "BT"): mark / is_visited in O(1).
 template <bool REGMASK>
@@ -75,14 +68,6 @@ struct Tabu {
         else
             return w[v >> 5];
     }
-    // Word q for q in [0, nw), read by the lane that scans it.
-    __device__ __forceinline__ uint32_t word_at(int q) const
-    {
-        if constexpr (REGMASK)
-            return reg;  // q == lane when n <= 1024
-        else
-            return w[q];
-    }
 };
 
 __device__ __forceinline__ uint32_t pick_word(const uint4 &r, int e)
@@ -90,57 +75,129 @@ __device__ __forceinline__ uint32_t pick_word(const uint4 &r, int e)
     return e == 0 ? r.x : (e == 1 ? r.y : (e == 2 ? r.z : r.w));
 }
 
-// Fallback when every candidate of `cur` is visited (fallback = 0): the
-// unvisited node with the largest choice_info, ties -> lower id.  With
-// fallback = 1: reservoir keys over all unvisited nodes (whole-row stream).
-template <bool REGMASK>
-__device__ __forceinline__ int fallback_pick(const ConstructArgs &a, const Tabu<REGMASK> tb,
-                                          int lane, int cur, int t, int ant, uint32_t it)
+__device__ __forceinline__ float pick_f(const float4 &r, int e)
 {
-    const float *row = a.wmat + (size_t)cur * a.ld;
-    uint32_t bk = 0, bj = 0xFFFFFFFFu;
-    for (int q0 = 0; q0 < tb.nw; q0 += 32) {
-        const int q = q0 + lane;
-        uint32_t un = 0;
-        if (q < tb.nw) {
-            un = ~tb.word_at(q);
-            if (q == tb.nw - 1 && (a.n & 31)) un &= (1u << (a.n & 31)) - 1u;
+    return e == 0 ? r.x : (e == 1 ? r.y : (e == 2 ? r.z : r.w));
+}
+
+// Score every unvisited node of `row` in 4-node chunks and return the winner
+// (ties -> lower id).  GREEDY: the key is the weight itself (the candidate-list
+// fallback of choice_info); otherwise the reservoir key log2(r) * inv-weight,
+// r from the whole-row stream, with `row` holding the reciprocal weights (RECIP)
+// or the weights.  Loads of four chunk-columns are issued before they are used.
+template <bool REGMASK, bool GREEDY, bool RECIP>
+__device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, uint32_t reg,
+                                        const uint32_t *w, int lane, uint32_t t, uint32_t ant,
+                                        uint32_t it, uint32_t k0, uint32_t k1, uint32_t *err,
+                                        int cur)
+{
+    const int nch = (n + 3) >> 2;
+    uint32_t bk = 0, bv = 0xFFFFFFFFu;
+    for (int c0 = 0; c0 < nch; c0 += 128) {
+        float4 w4[4];
+        uint32_t bits[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = c0 + 32 * u + lane;
+            const int v0 = c << 2;
+            const int vq = v0 < n ? v0 : n - 1;
+            uint32_t word;
+            if constexpr (REGMASK)
+                word = __shfl_sync(FULL, reg, (vq >> 5) & 31);
+            else
+                word = w[vq >> 5];
+            bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
+            w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        while (un) {
-            const int b = __ffs(un) - 1;
-            un &= un - 1;
-            const int j = (q << 5) + b;
-            const float w = __ldg(row + j);
-            uint32_t kk;
-            if (a.fallback == 0) {
-                kk = ord_key(w);
-            } else {
-                const uint4 r = philox10(make_uint4(0x80000000u | ((uint32_t)j >> 2), (uint32_t)t,
-                                                    (uint32_t)ant, it),
-                                         a.key0, a.key1);
-                const float lg = log2f(unit_open(pick_word(r, j & 3)));
-                kk = ord_key(__fmul_rn(lg, __frcp_rn(w)));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (bits[u] == 0xFu) continue;
+            const int v0 = (c0 + 32 * u + lane) << 2;
+            uint4 r = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (!GREEDY) {
+                r = make_uint4(0x80000000u | (uint32_t)(v0 >> 2), t, ant, it);
+                philox_rounds<0, 10>(r, k0, k1);
             }
-            if (kk > bk) {
-                bk = kk;
-                bj = (uint32_t)j;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int v = v0 + e;
+                if (v >= n || ((bits[u] >> e) & 1u)) continue;
+                const float x = pick_f(w4[u], e);
+                uint32_t kk;
+                if constexpr (GREEDY) {
+                    kk = ord_key(x);
+                } else {
+                    const float lg = log2f(unit_open(pick_word(r, e)));
+                    kk = ord_key(__fmul_rn(lg, RECIP ? x : __frcp_rn(x)));
+                }
+                if (kk > bk) {
+                    bk = kk;
+                    bv = (uint32_t)v;
+                }
             }
         }
     }
     const uint32_t mx = __reduce_max_sync(FULL, bk);
     if (mx == 0u) {
-        if (lane == 0) atomicOr(&a.sc->err, ERR_NO_UNVISITED);
+        if (lane == 0) atomicOr(err, ERR_NO_UNVISITED);
         return cur;
     }
-    return (int)__reduce_min_sync(FULL, bk == mx ? bj : 0xFFFFFFFFu);
+    return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
 }
+
+// Candidate-list fallback, out of line so the hot step stays compact:
+// fallback = 0 takes the unvisited node of largest choice_info, fallback = 1
+// reservoir-samples all unvisited nodes (whole-row stream).
+template <bool REGMASK>
+__device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, uint32_t reg,
+                                          const uint32_t *w, int lane, int mode, uint32_t t,
+                                          uint32_t ant, uint32_t it, uint32_t k0, uint32_t k1,
+                                          uint32_t *err, int cur)
+{
+    if (mode == 0)
+        return scan_row<REGMASK, true, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
+    return scan_row<REGMASK, false, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
+}
+
+// Per-ant tour window: lane l holds entry 32k + l of the current window; every
+// 32 steps the window is stored (one 128-byte row) and its edges are summed.
+template <bool XY>
+struct Window {
+    int twin = 0;       // this lane's entry
+    int prev_last = -1; // last entry of the previous window (-1: none)
+    int acc = 0;        // this lane's share of the tour length
+    int dpend = 0;      // explicit-matrix mode: edge length loaded last window
+
+    __device__ __forceinline__ void record(int lane, int t, int v)
+    {
+        if (lane == (t & 31)) twin = v;
+    }
+    // Window ending at step t_end (inclusive): store and add its edges.
+    __device__ __forceinline__ void flush(const ConstructArgs &a, int32_t *trow, int lane,
+                                          int t_end)
+    {
+        const int t0 = t_end & ~31, cnt = (t_end & 31) + 1;
+        if (lane < cnt) trow[t0 + lane] = twin;
+        int prev = __shfl_up_sync(FULL, twin, 1);
+        if (lane == 0) prev = prev_last;
+        const bool ok = lane < cnt && prev >= 0;
+        if constexpr (XY) {
+            if (ok) acc += euc2d_exact(__ldg(a.xy + prev), __ldg(a.xy + twin));
+        } else {
+            acc += dpend;
+            dpend = ok ? __ldg(a.dist + (size_t)prev * a.ld + twin) : 0;
+        }
+        prev_last = __shfl_sync(FULL, twin, 31);
+    }
+};
 
 // One candidate-list step: lane c scores slot c of cur's list.
 template <bool REGMASK>
-__device__ __forceinline__ int select_cand(const ConstructArgs &a, const uint16_t *cc,
-                                           const float *cw, const Tabu<REGMASK> &tb, int lane,
-                                           int cur, float lg, int t, int ant, uint32_t it,
-                                           uint32_t &fbn)
+__device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t *cc,
+                                         const float *cw, const Tabu<REGMASK> &tb, int lane,
+                                         int cur, float lg, int t, int ant, uint32_t it,
+                                         uint32_t &fbn)
 {
     const bool act = lane < a.cl;
     uint32_t v = 0;
@@ -154,57 +211,62 @@ __device__ __forceinline__ int select_cand(const ConstructArgs &a, const uint16_
     const bool ok = act && !((word >> (v & 31)) & 1u);
     const uint32_t k = ok ? ord_key(__fmul_rn(lg, wi)) : 0u;
     const uint32_t mx = __reduce_max_sync(FULL, k);
-    if (mx != 0u) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
+    if (__builtin_expect(mx != 0u, 1)) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
     ++fbn;
-    return fallback_pick<REGMASK>(a, tb, lane, cur, t, ant, it);
+    return cand_fallback<REGMASK>(a.wmat + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane, a.fallback,
+                                  (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur);
 }
 
-// One whole-row step: lane l scores nodes 4c..4c+3 for c = l, l + 32, ...
-template <bool REGMASK>
-__device__ __forceinline__ int select_row(const ConstructArgs &a, const float *W,
-                                          const Tabu<REGMASK> &tb, int lane, int cur, int t,
-                                          int ant, uint32_t it)
+// Four steps t = 4g .. 4g+3 with draws lg[0..3]; meanwhile the generator call of
+// group g+1 runs in slices and its log2s replace lg.  CHECK: skip t == 0 and
+// t >= n and flush windows here (first and last groups); otherwise the caller
+// flushes.
+template <bool CHECK, bool REGMASK, bool XY>
+__device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_t *cc,
+                                           const float *cw, Tabu<REGMASK> &tb, Window<XY> &win,
+                                           int32_t *trow, int lane, int ant, uint32_t it, int g,
+                                           float (&lg)[4], int &cur, uint32_t &fbn)
 {
-    const float *row = W + (size_t)cur * a.ld;
-    const int nch = (a.n + 3) >> 2;
-    uint32_t bk = 0, bv = 0xFFFFFFFFu;
-    for (int c0 = 0; c0 < nch; c0 += 32) {
-        const int c = c0 + lane;
-        const int v0 = c << 2;
-        const uint32_t word = tb.word_of(v0 < a.n ? v0 : a.n - 1);
-        if (c < nch) {
-            const uint32_t bits = (word >> (v0 & 31)) & 0xFu;
-            if (bits != 0xFu) {
-                const uint4 r = philox10(
-                    make_uint4(0x80000000u | (uint32_t)c, (uint32_t)t, (uint32_t)ant, it), a.key0,
-                    a.key1);
-                const float4 wi = *reinterpret_cast<const float4 *>(row + v0);
-                const float wv[4] = {wi.x, wi.y, wi.z, wi.w};
+    uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
+    float nl[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int v = v0 + e;
-                    if (v < a.n && !((bits >> e) & 1u)) {
-                        const float lg = log2f(unit_open(pick_word(r, e)));
-                        const uint32_t kk = ord_key(__fmul_rn(lg, wv[e]));
-                        if (kk > bk) {
-                            bk = kk;
-                            bv = (uint32_t)v;
-                        }
-                    }
-                }
-            }
+    for (int j = 0; j < 4; ++j) {
+        if (j == 0) philox_rounds<0, 4>(nx, a.key0, a.key1);
+        if (j == 1) philox_rounds<4, 8>(nx, a.key0, a.key1);
+        if (j == 2) {
+            philox_rounds<8, 10>(nx, a.key0, a.key1);
+            nl[0] = log2f(unit_open(nx.x));
+            nl[1] = log2f(unit_open(nx.y));
         }
+        if (j == 3) {
+            nl[2] = log2f(unit_open(nx.z));
+            nl[3] = log2f(unit_open(nx.w));
+        }
+        const int t = 4 * g + j;
+        if (CHECK && (t == 0 || t >= a.n)) continue;
+        const int next = cand_step<REGMASK>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
+        tb.mark(lane, next);
+        win.record(lane, t, next);
+        if (CHECK && ((t & 31) == 31 || t == a.n - 1)) win.flush(a, trow, lane, t);
+        cur = next;
     }
-    const uint32_t mx = __reduce_max_sync(FULL, bk);
-    if (mx == 0u) {
-        if (lane == 0) atomicOr(&a.sc->err, ERR_NO_UNVISITED);
-        return cur;
-    }
-    return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
+}
+
+// One whole-row step.
+template <bool REGMASK, bool STAGED>
+__device__ __forceinline__ int row_step(const ConstructArgs &a, const float *W,
+                                        const Tabu<REGMASK> &tb, int lane, int cur, int t,
+                                        int ant, uint32_t it)
+{
+    return scan_row<REGMASK, false, true>(W + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane,
+                                          (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1,
+                                          &a.sc->err, cur);
 }
 
 template <int MODE, bool STAGED, bool REGMASK, bool XY>
-__global__ void __launch_bounds__(1024, 1) k_construct(const ConstructArgs a)
+__global__ void __launch_bounds__(512, 1) k_construct(const ConstructArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
@@ -248,55 +310,57 @@ __global__ void __launch_bounds__(1024, 1) k_construct(const ConstructArgs a)
     const int stride = gridDim.x * warps;
     for (int ant = blockIdx.x * warps + warp; ant < a.m; ant += stride) {
         // Alg. 1: the first node is drawn uniformly
-        const uint4 s4 = philox10(make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it), a.key0, a.key1);
+        uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
+        philox_rounds<0, 10>(s4, a.key0, a.key1);
         const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
         tb.clear(lane);
         tb.mark(lane, start);
         int cur = start;
-        int twin = start;      // this lane's entry of the current 32-step window
-        int prev_last = -1;    // last node of the previous window
-        int acc = 0;           // this lane's share of the tour length
+        Window<XY> win;
+        win.twin = start;
         uint32_t fbn = 0;
         int32_t *trow = a.tours + (size_t)ant * a.ld;
 
-        for (int g = 0; (g << 2) < a.n; ++g) {
-            float lg0 = 0.f, lg1 = 0.f, lg2 = 0.f, lg3 = 0.f;
-            if constexpr (MODE == CAND) {
-                if (lane < a.cl) {
-                    const uint4 r = philox10(
-                        make_uint4((uint32_t)lane, (uint32_t)g, (uint32_t)ant, it), a.key0, a.key1);
-                    lg0 = log2f(unit_open(r.x));
-                    lg1 = log2f(unit_open(r.y));
-                    lg2 = log2f(unit_open(r.z));
-                    lg3 = log2f(unit_open(r.w));
-                }
+        if constexpr (MODE == CAND) {
+            float lg[4];
+            {
+                uint4 r = make_uint4((uint32_t)lane, 0u, (uint32_t)ant, it);
+                philox_rounds<0, 10>(r, a.key0, a.key1);
+                lg[0] = 0.0f;  // step 0 is the start node
+                lg[1] = log2f(unit_open(r.y));
+                lg[2] = log2f(unit_open(r.z));
+                lg[3] = log2f(unit_open(r.w));
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int t = (g << 2) + j;
-                if (t == 0) continue;
-                if (t >= a.n) break;
-                int next;
-                if constexpr (MODE == CAND) {
-                    const float lg = j == 0 ? lg0 : (j == 1 ? lg1 : (j == 2 ? lg2 : lg3));
-                    next = select_cand<REGMASK>(a, cc, cw, tb, lane, cur, lg, t, ant, it, fbn);
-                } else {
-                    next = select_row<REGMASK>(a, cw, tb, lane, cur, t, ant, it);
-                }
+            cand_group<true, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, 0, lg, cur, fbn);
+            int g = 1;
+            for (; 4 * g + 3 <= a.n - 1; ++g) {
+                cand_group<false, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, g, lg,
+                                               cur, fbn);
+                if ((g & 7) == 7) win.flush(a, trow, lane, 4 * g + 3);
+            }
+            if (4 * g <= a.n - 1) {
+                cand_group<true, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, g, lg, cur,
+                                              fbn);
+            } else if (g > 1 && ((g - 1) & 7) != 7) {
+                win.flush(a, trow, lane, a.n - 1);  // the last full group ended the tour
+            }
+        } else {
+            for (int t = 1; t < a.n; ++t) {
+                const int next = row_step<REGMASK, STAGED>(a, cw, tb, lane, cur, t, ant, it);
                 tb.mark(lane, next);
-                if (lane == (t & 31)) twin = next;
-                if ((t & 31) == 31 || t == a.n - 1) {
-                    const int t0 = t & ~31, cnt = (t & 31) + 1;
-                    if (lane < cnt) trow[t0 + lane] = twin;
-                    int prev = __shfl_up_sync(FULL, twin, 1);
-                    if (lane == 0) prev = prev_last;
-                    if (lane < cnt && prev >= 0) acc += edge_len<XY>(a, prev, twin);
-                    prev_last = __shfl_sync(FULL, twin, 31);
-                }
+                win.record(lane, t, next);
+                if ((t & 31) == 31 || t == a.n - 1) win.flush(a, trow, lane, t);
                 cur = next;
             }
         }
-        if (lane == 0) acc += edge_len<XY>(a, cur, start);  // close the cycle
+        // close the cycle, then collect the lanes' shares
+        int acc = win.acc;
+        if constexpr (XY) {
+            if (lane == 0) acc += euc2d_exact(__ldg(a.xy + cur), __ldg(a.xy + start));
+        } else {
+            acc += win.dpend;
+            if (lane == 0) acc += __ldg(a.dist + (size_t)cur * a.ld + start);
+        }
         const int total = (int)__reduce_add_sync(FULL, (unsigned)acc);
         if (lane == 0) {
             a.lens[ant] = total;
@@ -332,14 +396,17 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     plan->regmask = a.n <= 1024;
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
+    // staged: one CTA per SM (the table fills its shared memory) carrying
+    // ceil(m / #SMs) ants, at most 16 warps; warps loop over further ants
     int w = (a.m + num_sms - 1) / num_sms;
-    w = w < 1 ? 1 : (w > 32 ? 32 : w);
+    w = w < 1 ? 1 : (w > 16 ? 16 : w);
     const size_t masks = plan->regmask ? 0 : (size_t)w * nw * sizeof(uint32_t);
     const size_t need = table + 16 + masks;
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
         plan->warps = w;
-        plan->grid = (a.m + w - 1) / w;
+        const int g = (a.m + w - 1) / w;
+        plan->grid = g < num_sms ? g : num_sms;
         plan->smem = need;
     } else {
         plan->staged = 0;

@@ -52,6 +52,21 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// Rounds [R0, R1) of the same generator on counter c, for spreading one call
+// over several steps of a dependent chain (round r uses key + r * Weyl).
+template <int R0, int R1>
+__device__ __forceinline__ void philox_rounds(uint4 &c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = R0; r < R1; ++r) {
+        const uint32_t rk0 = k0 + (uint32_t)r * 0x9E3779B9u;
+        const uint32_t rk1 = k1 + (uint32_t)r * 0xBB67AE85u;
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ rk0, lo1, hi0 ^ c.w ^ rk1, lo0);
+    }
+}
+
 // r = ((x >> 9) + 1/2) * 2^-23, exactly representable, in (0, 1).
 __device__ __forceinline__ float unit_open(uint32_t x)
 {
@@ -67,13 +82,19 @@ __device__ __forceinline__ uint32_t ord_key(float f)
 }
 
 // TSPLIB rounded Euclidean distance nint(sqrt(s)), exact: q = floor(sqrt(s))
-// from a double square root corrected by integer comparisons, then
-// nint = q + [s > q^2 + q].  |coords| < 2^30 keeps s below 2^63.
+// from a floating-point square root corrected by integer comparisons, then
+// nint = q + [s > q^2 + q].  Below 2^48 a float square root is within 2 of q
+// (cheap on every SM); above it the double one is.  |coords| < 2^30 keeps s
+// below 2^63.
 __device__ __forceinline__ int32_t euc2d_exact(int2 a, int2 b)
 {
     const long long dx = (long long)a.x - b.x, dy = (long long)a.y - b.y;
     const unsigned long long s = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
-    unsigned long long q = (unsigned long long)sqrt((double)s);
+    unsigned long long q;
+    if (s < (1ull << 48))
+        q = (unsigned long long)__fsqrt_rn(__ull2float_rn(s));
+    else
+        q = (unsigned long long)sqrt((double)s);
     while (q * q > s) --q;
     while ((q + 1) * (q + 1) <= s) ++q;
     return (int32_t)(q + (s > q * q + q ? 1ull : 0ull));
