@@ -249,7 +249,8 @@ def run_ours(args, w):
     _build.build()
     xy = _instance(w)
     seed = 1 + rank
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # the flush, the colony and all timing share this stream
     col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev,
                  stream=stream.cuda_stream, **PARAMS)
     col.enable_phase_timing(True)

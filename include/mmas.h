@@ -75,7 +75,8 @@ typedef struct {
  *            0: take the unvisited node of largest choice_info (ties -> lower id);
  *            1: reservoir-sample all unvisited nodes                (0)
  *   device   CUDA device ordinal                                   (0)
- *   stream   cudaStream_t to enqueue on, or NULL for a private stream (NULL)
+ *   stream   cudaStream_t to enqueue on, or NULL for a private non-blocking
+ *            stream; pass cudaStreamLegacy to use the legacy default stream (NULL)
  *
  * Random draws: start node of ant k in iteration it = word 0 of
  * Philox(ctr = (0xFFFFFFFF, 0, k, it)); candidate slot s at step t = word

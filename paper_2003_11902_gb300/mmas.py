@@ -113,11 +113,18 @@ def _check(h, status):
         raise MMASError(status, msg.decode() if msg else "")
 
 
+CUDA_STREAM_LEGACY = 1  # the value of cudaStreamLegacy
+
+
 def _torch_stream():
+    """PyTorch's current stream as a cudaStream_t value.  Its default stream has
+    handle 0, which the C ABI reads as "make a private stream", so it is passed
+    as cudaStreamLegacy to keep the library ordered with PyTorch's work."""
     try:
         import torch
         if torch.cuda.is_available():
-            return torch.cuda.current_stream().cuda_stream
+            h = torch.cuda.current_stream().cuda_stream
+            return h if h else CUDA_STREAM_LEGACY
     except Exception:
         pass
     return None
@@ -248,6 +255,8 @@ class Colony:
         p.cl, p.seed, p.deposit, p.fallback, p.device = cl, int(seed), deposit, fallback, device
         if stream == "torch":
             stream = _torch_stream()
+        elif stream == 0:
+            stream = CUDA_STREAM_LEGACY
         p.stream = stream
         self.n, self.m, self.cl = n, p.m, cl
         self._h = mmas_create(xy=xy, dist=dist, params=p)
