@@ -1,17 +1,17 @@
-// Solution construction (Alg. 1, inner loops) with tour lengths fused in.
+// Solution construction (Alg. 1, inner loops).
 //
 // One warp builds one ant's tour.  At each of the n-1 steps the warp scores the
 // unvisited nodes of Eq. (1)'s neighbourhood with weighted-reservoir keys
 // log2(r) / w (Alg. 4, Sec. 4.2.2), reduces them with one redux.max and one
 // redux.min (ties -> lower node id), marks the winner in a bitmask tabu
-// (Sec. 4.1) and appends it to the tour.
+// (Sec. 4.1) and appends it to the tour.  Tour lengths are computed afterwards
+// by the scoring kernel, off this dependency chain.
 //
 //  - Candidate-list mode (cl in 1..32, Sec. 4.3): lane c scores candidate
 //    slot c.  A slot's uniform depends on (iteration, ant, step, slot) only, so
-//    one Philox call yields the draws of four consecutive steps, and the call
-//    for the next four steps (and its log2s) is spread over the current four
-//    steps, filling the latency of the step-to-step dependency chain.  When
-//    every candidate is visited, an out-of-line fallback scans the row.
+//    one Philox call yields the draws of four consecutive steps; the call for
+//    the next four steps and its log2s are spread over the current four steps.
+//    When every candidate is visited, an out-of-line fallback scans the row.
 //  - Whole-row mode (cl = 0): lane l scores nodes 4c..4c+3 for c = l, l+32, ...,
 //    reading 16 bytes of 1/choice_info per chunk, one Philox call per chunk.
 //
@@ -19,10 +19,8 @@
 // reciprocal weight matrix) is copied into shared memory once per CTA with the
 // bulk-copy engine when it fits; each CTA then runs ceil(m / #SMs) ants.
 // The tabu of an ant lives in registers (lane l holds nodes 32l..32l+31) when
-// n <= 1024, otherwise in the warp's slice of shared memory.
-// Tour entries are buffered one per lane and written as 128-byte rows every 32
-// steps; each lane then adds the length of its edge (coordinates: computed
-// exactly in registers; explicit matrix: loaded one window ahead of its use).
+// n <= 1024, otherwise in the warp's slice of shared memory.  Tour entries are
+// buffered one per lane and written as 128-byte rows every 32 steps.
 #include "internal.cuh"
 
 namespace mmas {
@@ -54,7 +52,8 @@ struct Tabu {
     __device__ __forceinline__ void mark(int lane, int v)
     {
         if constexpr (REGMASK) {
-            if (lane == (v >> 5)) reg |= 1u << (v & 31);
+            // select, not a branch: a one-lane branch diverges the warp
+            reg |= ((v >> 5) == lane) ? (1u << (v & 31)) : 0u;
         } else {
             if (lane == 0) w[v >> 5] |= 1u << (v & 31);
             __syncwarp();
@@ -82,22 +81,24 @@ __device__ __forceinline__ float pick_f(const float4 &r, int e)
 
 // Score every unvisited node of `row` in 4-node chunks and return the winner
 // (ties -> lower id).  GREEDY: the key is the weight itself (the candidate-list
-// fallback of choice_info); otherwise the reservoir key log2(r) * inv-weight,
+// fallback on choice_info); otherwise the reservoir key log2(r) * inv-weight,
 // r from the whole-row stream, with `row` holding the reciprocal weights (RECIP)
-// or the weights.  Loads of four chunk-columns are issued before they are used.
+// or the weights.  Eight chunk-columns (1024 nodes) are loaded before use, so
+// rows of up to 1024 nodes cost one memory round trip.
 template <bool REGMASK, bool GREEDY, bool RECIP>
 __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, uint32_t reg,
                                         const uint32_t *w, int lane, uint32_t t, uint32_t ant,
                                         uint32_t it, uint32_t k0, uint32_t k1, uint32_t *err,
                                         int cur)
 {
+    constexpr int U = 8;
     const int nch = (n + 3) >> 2;
     uint32_t bk = 0, bv = 0xFFFFFFFFu;
-    for (int c0 = 0; c0 < nch; c0 += 128) {
-        float4 w4[4];
-        uint32_t bits[4];
+    for (int c0 = 0; c0 < nch; c0 += 32 * U) {
+        float4 w4[U];
+        uint32_t bits[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int c = c0 + 32 * u + lane;
             const int v0 = c << 2;
             const int vq = v0 < n ? v0 : n - 1;
@@ -111,7 +112,7 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, ui
                             : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
             if (bits[u] == 0xFu) continue;
             const int v0 = (c0 + 32 * u + lane) << 2;
             uint4 r = make_uint4(0u, 0u, 0u, 0u);
@@ -146,6 +147,55 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, ui
     return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
 }
 
+// Greedy fallback: the unvisited node of largest choice_info (ties -> lower
+// id).  Each lane walks the unvisited bits of its own bitmask words (lane l
+// owns words l, l+32, ...), loading up to eight weights per round trip, so the
+// cost follows the number of unvisited nodes, not n.
+template <bool REGMASK>
+__device__ __forceinline__ int greedy_unvisited(const float *__restrict__ row, int n, uint32_t reg,
+                                                const uint32_t *w, int lane, uint32_t *err,
+                                                int cur)
+{
+    const int nw = (n + 31) >> 5;
+    uint32_t bk = 0, bv = 0xFFFFFFFFu;
+    for (int q0 = 0; q0 < nw; q0 += 32) {
+        const int q = q0 + lane;
+        uint32_t un = 0;
+        if (q < nw) {
+            un = ~(REGMASK ? reg : w[q]);
+            if (q == nw - 1 && (n & 31)) un &= (1u << (n & 31)) - 1u;
+        }
+        while (un) {
+            int j[8];
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                j[u] = -1;
+                if (un) {
+                    j[u] = (q << 5) + __ffs(un) - 1;
+                    un &= un - 1;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = j[u] >= 0 ? __ldg(row + j[u]) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t kk = j[u] >= 0 ? ord_key(x[u]) : 0u;
+                if (kk > bk) {  // ids increase within a lane: strict '>' keeps the lower id
+                    bk = kk;
+                    bv = (uint32_t)j[u];
+                }
+            }
+        }
+    }
+    const uint32_t mx = __reduce_max_sync(FULL, bk);
+    if (mx == 0u) {
+        if (lane == 0) atomicOr(err, ERR_NO_UNVISITED);
+        return cur;
+    }
+    return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+}
+
 // Candidate-list fallback, out of line so the hot step stays compact:
 // fallback = 0 takes the unvisited node of largest choice_info, fallback = 1
 // reservoir-samples all unvisited nodes (whole-row stream).
@@ -155,42 +205,9 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
                                           uint32_t ant, uint32_t it, uint32_t k0, uint32_t k1,
                                           uint32_t *err, int cur)
 {
-    if (mode == 0)
-        return scan_row<REGMASK, true, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
+    if (mode == 0) return greedy_unvisited<REGMASK>(row, n, reg, w, lane, err, cur);
     return scan_row<REGMASK, false, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
 }
-
-// Per-ant tour window: lane l holds entry 32k + l of the current window; every
-// 32 steps the window is stored (one 128-byte row) and its edges are summed.
-template <bool XY>
-struct Window {
-    int twin = 0;       // this lane's entry
-    int prev_last = -1; // last entry of the previous window (-1: none)
-    int acc = 0;        // this lane's share of the tour length
-    int dpend = 0;      // explicit-matrix mode: edge length loaded last window
-
-    __device__ __forceinline__ void record(int lane, int t, int v)
-    {
-        if (lane == (t & 31)) twin = v;
-    }
-    // Window ending at step t_end (inclusive): store and add its edges.
-    __device__ __forceinline__ void flush(const ConstructArgs &a, int32_t *trow, int lane,
-                                          int t_end)
-    {
-        const int t0 = t_end & ~31, cnt = (t_end & 31) + 1;
-        if (lane < cnt) trow[t0 + lane] = twin;
-        int prev = __shfl_up_sync(FULL, twin, 1);
-        if (lane == 0) prev = prev_last;
-        const bool ok = lane < cnt && prev >= 0;
-        if constexpr (XY) {
-            if (ok) acc += euc2d_exact(__ldg(a.xy + prev), __ldg(a.xy + twin));
-        } else {
-            acc += dpend;
-            dpend = ok ? __ldg(a.dist + (size_t)prev * a.ld + twin) : 0;
-        }
-        prev_last = __shfl_sync(FULL, twin, 31);
-    }
-};
 
 // One candidate-list step: lane c scores slot c of cur's list.
 template <bool REGMASK>
@@ -217,18 +234,25 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
                                   (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur);
 }
 
-// Four steps t = 4g .. 4g+3 with draws lg[0..3]; meanwhile the generator call of
-// group g+1 runs in slices and its log2s replace lg.  CHECK: skip t == 0 and
-// t >= n and flush windows here (first and last groups); otherwise the caller
-// flushes.
-template <bool CHECK, bool REGMASK, bool XY>
+// Store the window of steps [32w, t_end]: lane l holds entry 32w + l.
+__device__ __forceinline__ void store_window(int32_t *trow, int lane, int w, int t_end, int twin)
+{
+    if (lane <= t_end - 32 * w) trow[32 * w + lane] = twin;
+}
+
+// Four steps t = 4g .. 4g+3 with draws lg[0..3]; meanwhile the generator call
+// of group g+1 runs in slices and its log2s replace lg.  CHECK: skip t == 0 and
+// t >= n and store windows here (first and last groups); otherwise the caller
+// stores the window after every eighth group.
+template <bool CHECK, bool REGMASK>
 __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_t *cc,
-                                           const float *cw, Tabu<REGMASK> &tb, Window<XY> &win,
-                                           int32_t *trow, int lane, int ant, uint32_t it, int g,
-                                           float (&lg)[4], int &cur, uint32_t &fbn)
+                                           const float *cw, Tabu<REGMASK> &tb, int32_t *trow,
+                                           int lane, int ant, uint32_t it, int g, float (&lg)[4],
+                                           int &cur, int &twin, uint32_t &fbn)
 {
     uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
     float nl[4];
+    const int tb32 = (4 * g) & 31;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j == 0) philox_rounds<0, 4>(nx, a.key0, a.key1);
@@ -246,30 +270,20 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
         if (CHECK && (t == 0 || t >= a.n)) continue;
         const int next = cand_step<REGMASK>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
         tb.mark(lane, next);
-        win.record(lane, t, next);
-        if (CHECK && ((t & 31) == 31 || t == a.n - 1)) win.flush(a, trow, lane, t);
+        twin = (lane == tb32 + j) ? next : twin;
+        if (CHECK && ((t & 31) == 31 || t == a.n - 1)) store_window(trow, lane, t >> 5, t, twin);
         cur = next;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) lg[j] = nl[j];
 }
 
-// One whole-row step.
-template <bool REGMASK, bool STAGED>
-__device__ __forceinline__ int row_step(const ConstructArgs &a, const float *W,
-                                        const Tabu<REGMASK> &tb, int lane, int cur, int t,
-                                        int ant, uint32_t it)
-{
-    return scan_row<REGMASK, false, true>(W + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane,
-                                          (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1,
-                                          &a.sc->err, cur);
-}
-
-template <int MODE, bool STAGED, bool REGMASK, bool XY>
-__global__ void __launch_bounds__(512, 1) k_construct(const ConstructArgs a)
+template <int MODE, bool STAGED, bool REGMASK>
+__global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t it = (uint32_t)a.iter[0];
 
     const float *cw = (MODE == CAND) ? a.cwinv : a.wmat;
     const uint16_t *cc = a.cand16;
@@ -306,9 +320,8 @@ __global__ void __launch_bounds__(512, 1) k_construct(const ConstructArgs a)
     tb.nw = (a.n + 31) >> 5;
     if constexpr (!REGMASK) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
 
-    const uint32_t it = (uint32_t)a.iter[0];
-    const int stride = gridDim.x * warps;
-    for (int ant = blockIdx.x * warps + warp; ant < a.m; ant += stride) {
+    const int stride = gridDim.x * cons_warps;
+    for (int ant = blockIdx.x * cons_warps + warp; ant < a.m; ant += stride) {
         // Alg. 1: the first node is drawn uniformly
         uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
         philox_rounds<0, 10>(s4, a.key0, a.key1);
@@ -316,8 +329,7 @@ __global__ void __launch_bounds__(512, 1) k_construct(const ConstructArgs a)
         tb.clear(lane);
         tb.mark(lane, start);
         int cur = start;
-        Window<XY> win;
-        win.twin = start;
+        int twin = start;  // lane l holds entry 32w + l of the current window
         uint32_t fbn = 0;
         int32_t *trow = a.tours + (size_t)ant * a.ld;
 
@@ -331,59 +343,43 @@ __global__ void __launch_bounds__(512, 1) k_construct(const ConstructArgs a)
                 lg[2] = log2f(unit_open(r.z));
                 lg[3] = log2f(unit_open(r.w));
             }
-            cand_group<true, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, 0, lg, cur, fbn);
+            cand_group<true, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
             int g = 1;
             for (; 4 * g + 3 <= a.n - 1; ++g) {
-                cand_group<false, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, g, lg,
-                                               cur, fbn);
-                if ((g & 7) == 7) win.flush(a, trow, lane, 4 * g + 3);
+                cand_group<false, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin,
+                                           fbn);
+                if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
             }
-            if (4 * g <= a.n - 1) {
-                cand_group<true, REGMASK, XY>(a, cc, cw, tb, win, trow, lane, ant, it, g, lg, cur,
-                                              fbn);
-            } else if (g > 1 && ((g - 1) & 7) != 7) {
-                win.flush(a, trow, lane, a.n - 1);  // the last full group ended the tour
-            }
+            if (4 * g <= a.n - 1)
+                cand_group<true, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
+            else if (g > 1 && ((g - 1) & 7) != 7)
+                store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
         } else {
             for (int t = 1; t < a.n; ++t) {
-                const int next = row_step<REGMASK, STAGED>(a, cw, tb, lane, cur, t, ant, it);
+                const int next = scan_row<REGMASK, false, true>(
+                    cw + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane, (uint32_t)t, (uint32_t)ant,
+                    it, a.key0, a.key1, &a.sc->err, cur);
                 tb.mark(lane, next);
-                win.record(lane, t, next);
-                if ((t & 31) == 31 || t == a.n - 1) win.flush(a, trow, lane, t);
+                twin = (lane == (t & 31)) ? next : twin;
+                if ((t & 31) == 31 || t == a.n - 1) store_window(trow, lane, t >> 5, t, twin);
                 cur = next;
             }
         }
-        // close the cycle, then collect the lanes' shares
-        int acc = win.acc;
-        if constexpr (XY) {
-            if (lane == 0) acc += euc2d_exact(__ldg(a.xy + cur), __ldg(a.xy + start));
-        } else {
-            acc += win.dpend;
-            if (lane == 0) acc += __ldg(a.dist + (size_t)cur * a.ld + start);
-        }
-        const int total = (int)__reduce_add_sync(FULL, (unsigned)acc);
-        if (lane == 0) {
-            a.lens[ant] = total;
-            if (fbn) atomicAdd(&a.sc->fallback_steps, (unsigned long long)fbn);
-        }
+        if (lane == 0 && fbn) atomicAdd(&a.sc->fallback_steps, (unsigned long long)fbn);
     }
 }
 
-using KernelFn = void (*)(const ConstructArgs);
+using KernelFn = void (*)(const ConstructArgs, int);
 
-KernelFn pick_kernel(int mode, int staged, int regmask, int xy)
+KernelFn pick_kernel(int mode, int staged, int regmask)
 {
-    static const KernelFn table[16] = {
-        k_construct<CAND, false, false, false>, k_construct<CAND, false, false, true>,
-        k_construct<CAND, false, true, false>,  k_construct<CAND, false, true, true>,
-        k_construct<CAND, true, false, false>,  k_construct<CAND, true, false, true>,
-        k_construct<CAND, true, true, false>,   k_construct<CAND, true, true, true>,
-        k_construct<ROW, false, false, false>,  k_construct<ROW, false, false, true>,
-        k_construct<ROW, false, true, false>,   k_construct<ROW, false, true, true>,
-        k_construct<ROW, true, false, false>,   k_construct<ROW, true, false, true>,
-        k_construct<ROW, true, true, false>,    k_construct<ROW, true, true, true>,
+    static const KernelFn table[8] = {
+        k_construct<CAND, false, false>, k_construct<CAND, false, true>,
+        k_construct<CAND, true, false>,  k_construct<CAND, true, true>,
+        k_construct<ROW, false, false>,  k_construct<ROW, false, true>,
+        k_construct<ROW, true, false>,   k_construct<ROW, true, true>,
     };
-    return table[(mode << 3) | (staged << 2) | (regmask << 1) | xy];
+    return table[(mode << 2) | (staged << 1) | regmask];
 }
 
 }  // namespace
@@ -397,24 +393,26 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
     // staged: one CTA per SM (the table fills its shared memory) carrying
-    // ceil(m / #SMs) ants, at most 16 warps; warps loop over further ants
+    // ceil(m / #SMs) ants, at most 12 warps; warps loop over further ants
     int w = (a.m + num_sms - 1) / num_sms;
-    w = w < 1 ? 1 : (w > 16 ? 16 : w);
+    w = w < 1 ? 1 : (w > 12 ? 12 : w);
     const size_t masks = plan->regmask ? 0 : (size_t)w * nw * sizeof(uint32_t);
     const size_t need = table + 16 + masks;
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
-        plan->warps = w;
+        plan->cons_warps = w;
+        plan->gen_warps = 0;
         const int g = (a.m + w - 1) / w;
         plan->grid = g < num_sms ? g : num_sms;
         plan->smem = need;
     } else {
         plan->staged = 0;
-        plan->warps = 4;
+        plan->cons_warps = 4;
+        plan->gen_warps = 0;
         plan->grid = (a.m + 3) / 4;
         plan->smem = plan->regmask ? 0 : (size_t)4 * nw * sizeof(uint32_t);
     }
-    KernelFn k = pick_kernel(row ? ROW : CAND, plan->staged, plan->regmask, a.xy != nullptr);
+    KernelFn k = pick_kernel(row ? ROW : CAND, plan->staged, plan->regmask);
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
 }
@@ -429,8 +427,8 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
         b.stage_w_bytes = (uint32_t)((size_t)a.n * a.ld * sizeof(float));
         b.stage_c_bytes = 0;
     }
-    KernelFn k = pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.regmask, a.xy != nullptr);
-    k<<<plan.grid, plan.warps * 32, plan.smem, s>>>(b);
+    KernelFn k = pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.regmask);
+    k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ struct Scalars {
     float delta;           // deposit amount of the pending update (float 1/C)
     int32_t dep_len;       // length of the tour being deposited
     uint32_t err;          // ERR_* bits
-    int32_t pad0;
+    uint32_t done;         // CTAs of the scoring kernel that finished (last-block election)
     unsigned long long fallback_steps;  // cumulative candidate-list fallbacks
     long long nn_len;      // nearest-neighbour tour length
     long long iterations;  // completed iterations
@@ -190,10 +190,7 @@ struct ConstructArgs {
     const uint16_t *cand16;    // [n][cl] candidate ids
     const float *cwinv;        // [n][cl] 1 / choice_info of each candidate
     const float *wmat;         // [n][ld] choice_info (cl > 0) or 1/choice_info (cl == 0)
-    const int2 *xy;            // [n] coordinates, or nullptr (then dist is used)
-    const int32_t *dist;       // [n][ld]
     int32_t *tours;            // [m][ld]
-    int32_t *lens;             // [m]
     Scalars *sc;
     uint32_t stage_w_bytes;    // bytes of the staged weight table (16-byte multiple)
     uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
@@ -202,7 +199,8 @@ struct ConstructArgs {
 struct ConstructPlan {
     int staged;     // stage the weight (and id) tables in shared memory
     int regmask;    // tabu bitmask held in registers (n <= 1024)
-    int warps;      // warps (= ants in flight) per CTA
+    int cons_warps; // warps building tours (one ant each) per CTA
+    int gen_warps;  // reserved (0)
     int grid;
     size_t smem;    // dynamic shared memory bytes
 };
@@ -216,6 +214,15 @@ struct BestArgs {
     int32_t *gb_tour;      // [n]
     int2 *nbr;             // [n]: successor and predecessor in the deposited tour
     Scalars *sc;
+};
+
+struct ScoreArgs {
+    int32_t n, m, ld, best;
+    const int32_t *tours;  // [m][ld]
+    const int2 *xy;        // coordinates, or nullptr (then dist)
+    const int32_t *dist;   // [n][ld]
+    int32_t *lens;         // [m]
+    BestArgs b;            // used by the last CTA when best != 0
 };
 
 struct UpdateArgs {
@@ -251,6 +258,7 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s);
 
 cudaError_t launch_best(const BestArgs &a, cudaStream_t s);
+cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s);
 
 }  // namespace mmas

@@ -1,5 +1,7 @@
 // The rest of an iteration after construction (Alg. 1; Sec. 2.1, Sec. 4.4):
-//   k_best    iteration best (shortest tour, ties -> lower ant), global best
+//   k_score   tour lengths (exact integer distances, one CTA per ant), then
+//             in its last CTA:
+//   select_best  iteration best (shortest tour, ties -> lower ant), global best
 //             replaced by a strictly shorter tour, trail limits, the deposit
 //             amount 1/C and each node's two neighbours in the deposited tour;
 //   k_update  one streaming pass over the n x n matrices: evaporation with
@@ -29,14 +31,20 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return v;
 }
 
-__global__ void __launch_bounds__(1024) k_best(const BestArgs a)
+// Iteration best, global best, limits, deposit amount and the deposited tour's
+// neighbours; run by ONE CTA (any multiple of 32 threads up to 1024).  Two
+// dependent memory rounds: the lengths (and the current global best), then the
+// chosen tour, which is copied and turned into neighbours in the same pass.
+__device__ void select_best(const BestArgs &a)
 {
     __shared__ unsigned long long red[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    Scalars *sc = a.sc;
+    const int gb = *((volatile int *)&sc->gb_len);
     unsigned long long best = ~0ull;
     for (int k = tid; k < a.m; k += blockDim.x) {
         const unsigned long long key =
-            ((unsigned long long)(uint32_t)a.lens[k] << 32) | (uint32_t)k;
+            ((unsigned long long)(uint32_t)__ldcg(a.lens + k) << 32) | (uint32_t)k;
         best = key < best ? key : best;
     }
     best = warp_min_u64(best);
@@ -51,14 +59,19 @@ __global__ void __launch_bounds__(1024) k_best(const BestArgs a)
     const unsigned long long b = red[0];
     const int ib = (int)(b & 0xFFFFFFFFull);
     const int len = (int)(b >> 32);
-    Scalars *sc = a.sc;
-    const int gb = sc->gb_len;
     const bool improved = len < gb;
-    __syncthreads();  // every thread has read gb_len before it changes
 
-    const int32_t *ibt = a.tours + (size_t)ib * a.ld;
-    if (improved)
-        for (int t = tid; t < a.n; t += blockDim.x) a.gb_tour[t] = ibt[t];
+    // deposit on the iteration best, or on the global best (which is the
+    // iteration best when it improved)
+    const bool from_ib = a.deposit == 0 || improved;
+    const int32_t *dep = from_ib ? a.tours + (size_t)ib * a.ld : a.gb_tour;
+    for (int t = tid; t < a.n; t += blockDim.x) {
+        const int v = dep[t];
+        const int nx = dep[t + 1 == a.n ? 0 : t + 1];
+        const int pv = dep[t == 0 ? a.n - 1 : t - 1];
+        a.nbr[v] = make_int2(nx, pv);
+        if (improved) a.gb_tour[t] = v;
+    }
     if (tid == 0) {
         sc->ib_len = len;
         sc->ib_ant = ib;
@@ -77,14 +90,63 @@ __global__ void __launch_bounds__(1024) k_best(const BestArgs a)
             sc->iterations += 1;
         }
     }
-    __syncthreads();  // the global-best copy is complete
-    const int32_t *dep = a.deposit ? a.gb_tour : ibt;
-    for (int t = tid; t < a.n; t += blockDim.x) {
-        const int v = dep[t];
-        const int nx = dep[t + 1 == a.n ? 0 : t + 1];
-        const int pv = dep[t == 0 ? a.n - 1 : t - 1];
-        a.nbr[v] = make_int2(nx, pv);
+}
+
+__global__ void __launch_bounds__(1024) k_best(const BestArgs a) { select_best(a); }
+
+// Tour lengths, then -- when a.best -- the last CTA to finish runs select_best
+// on all m lengths.  One CTA per ant; each thread takes four consecutive edges
+// per round (an int4 of the tour plus the following node) and issues all of
+// their loads before using them.  Distances are the exact integer ones.
+template <bool XY>
+__global__ void __launch_bounds__(256) k_score(const ScoreArgs a)
+{
+    __shared__ int red[8];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int acc = 0;
+    for (int ant = blockIdx.x; ant < a.m; ant += gridDim.x) {
+        const int32_t *tr = a.tours + (size_t)ant * a.ld;
+        int part = 0;
+        for (int q = tid; 4 * q < a.n; q += blockDim.x) {
+            const int t0 = 4 * q;
+            const int4 u4 = *reinterpret_cast<const int4 *>(tr + t0);  // ld is a multiple of 32
+            const int nx = tr[t0 + 4 < a.n ? t0 + 4 : 0];
+            const int node[5] = {u4.x, u4.y, u4.z, u4.w, nx};
+            const int cnt = a.n - t0 < 4 ? a.n - t0 : 4;  // edges t0 .. t0+cnt-1
+            // edge e joins node[e] and node[e+1]; the last real edge closes on nx
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (e >= cnt) break;
+                const int from = node[e];
+                const int to = (e + 1 < cnt) ? node[e + 1] : nx;
+                if constexpr (XY)
+                    part += euc2d_exact(__ldg(a.xy + from), __ldg(a.xy + to));
+                else
+                    part += __ldg(a.dist + (size_t)from * a.ld + to);
+            }
+        }
+        part = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        if (tid == 0) {
+            int sum = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
+            a.lens[ant] = sum;
+        }
+        __syncthreads();
+        acc += part;
     }
+    (void)acc;
+    if (!a.best) return;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.b.sc->done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    select_best(a.b);
+    if (tid == 0) a.b.sc->done = 0;
 }
 
 template <bool FULLROW, bool ALPHA1>
@@ -145,6 +207,17 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs a)
 cudaError_t launch_best(const BestArgs &a, cudaStream_t s)
 {
     k_best<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s)
+{
+    // one CTA per ant, at most 16 resident per SM's worth; CTAs loop over ants
+    int grid = a.m < num_sms * 8 ? a.m : num_sms * 8;
+    if (a.xy)
+        k_score<true><<<grid, 256, 0, s>>>(a);
+    else
+        k_score<false><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

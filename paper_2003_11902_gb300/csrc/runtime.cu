@@ -49,6 +49,7 @@ struct mmas_handle {
     ConstructArgs cargs{};
     ConstructPlan cplan{};
     BestArgs bargs{};
+    ScoreArgs sargs{};
     UpdateArgs uargs{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -183,7 +184,7 @@ mmas_status capture_iteration(mmas_handle *h)
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[0], cs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_construct(h->cargs, h->cplan, cs);
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[1], cs, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_best(h->bargs, cs);
+    if (e == cudaSuccess) e = launch_score(h->sargs, h->num_sms, cs);
     if (e == cudaSuccess) e = launch_update(h->uargs, h->num_sms, cs);
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[2], cs, cudaEventRecordExternal);
     cudaGraph_t g = nullptr;
@@ -289,7 +290,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.key1 = (uint32_t)(h->p.seed >> 32);
     ca.iter = &h->sc->iter;
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
-    ca.xy = h->xy; ca.dist = h->dist; ca.tours = h->tours; ca.lens = h->lens; ca.sc = h->sc;
+    ca.tours = h->tours; ca.sc = h->sc;
     ca.stage_w_bytes = (uint32_t)cw_bytes;
     ca.stage_c_bytes = (uint32_t)cc_bytes;
     if (cl == 0) { ca.stage_w_bytes = 0; ca.stage_c_bytes = 0; }
@@ -299,6 +300,10 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ba.n = n; ba.m = m; ba.ld = ld; ba.deposit = h->p.deposit; ba.advance = 1;
     ba.rho = (double)h->p.rho; ba.p_root = h->p_root;
     ba.lens = h->lens; ba.tours = h->tours; ba.gb_tour = h->gb_tour; ba.nbr = h->nbr; ba.sc = h->sc;
+
+    ScoreArgs &sa = h->sargs;
+    sa.n = n; sa.m = m; sa.ld = ld; sa.best = 1;
+    sa.tours = h->tours; sa.xy = h->xy; sa.dist = h->dist; sa.lens = h->lens; sa.b = ba;
 
     UpdateArgs &ua = h->uargs;
     ua.n = n; ua.ld = ld; ua.cl = cl; ua.fullrow = cl == 0; ua.evaporate = 1;
@@ -422,6 +427,9 @@ mmas_status mmas_construct(mmas_handle *h)
     if (check_handle(h)) return MMAS_EINVAL;
     DeviceGuard g(h->device);
     CK(h, launch_construct(h->cargs, h->cplan, h->stream));
+    ScoreArgs sa = h->sargs;
+    sa.best = 0;
+    CK(h, launch_score(sa, h->num_sms, h->stream));
     return MMAS_OK;
 }
 
@@ -539,7 +547,7 @@ mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out)
     out->tau_min = s.tmin;
     out->tau_max = s.tmax;
     out->construct_grid = h->cplan.grid;
-    out->construct_block = h->cplan.warps * 32;
+    out->construct_block = (h->cplan.cons_warps + h->cplan.gen_warps) * 32;
     out->construct_staged = h->cplan.staged;
     out->construct_smem = (int32_t)h->cplan.smem;
     out->row_pitch = h->ld;
