@@ -199,6 +199,42 @@ mmas_status mmas_enable_phase_timing(mmas_handle *h, int32_t enable);
  * timed iteration has run. */
 mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms, float *total_ms);
 
+/* ---- allocation-free scoring ----------------------------------------------
+ *
+ * For callers that must not have a library allocate device memory: serving
+ * loops that cannot afford cudaMalloc/cudaFree (they synchronise the whole
+ * device and stall every other stream), and frameworks whose caching allocator
+ * owns the device memory budget.  The paper has no counterpart; it is a service
+ * of this library.
+ *
+ * mmas_score_tours_noalloc computes, for m tours already in device memory, the
+ * length of each tour (TSPLIB rounded Euclidean distances, exact integers) and
+ * the shortest one, exactly as the iteration-best step does, but with no
+ * handle and without allocating: the caller passes every input and output, and
+ * the only scratch is a fixed array inside the library (one 8-byte partial
+ * minimum per CTA for at most 4,096 CTAs, plus a counter: about 33 KB per GPU,
+ * held from library load until the process exits).
+ *   d_tours  device, m x pitch int32; row k's first n entries are a tour (a
+ *            permutation of 0..n-1)
+ *   m        1 <= m <= MMAS_NOALLOC_MAX_ANTS
+ *   n        3 <= n <= 65535;  pitch >= n (elements per row)
+ *   d_xy     device, n x 2 int32 coordinates, |x|, |y| < 2^30
+ *   d_lens   device, m int32 (out): tour lengths; n * max(d) must be < 2^31
+ *   d_best   device, 2 int32 (out): {shortest length, lowest ant reaching it}
+ *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream)
+ * Asynchronous: the results are ready when the stream reaches them.
+ * Errors: EINVAL for a NULL buffer or a size out of range (checked before any
+ * GPU work, message in mmas_last_error(NULL)); ECUDA if a CUDA call fails.
+ * The first call on each device looks up the scratch's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the scratch and a call leaves it holding its own partial
+ * results, so calls whose GPU work may overlap (e.g. on different streams
+ * with no ordering between them) race and must be serialised by the caller. */
+#define MMAS_NOALLOC_MAX_ANTS 1048576
+mmas_status mmas_score_tours_noalloc(const int32_t *d_tours, int32_t m, int32_t n, int32_t pitch,
+                                     const int32_t *d_xy, int32_t *d_lens, int32_t *d_best,
+                                     void *stream);
+
 #ifdef __cplusplus
 }
 #endif

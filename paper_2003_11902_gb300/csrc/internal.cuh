@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mmas {
 
 // ---------------------------------------------------------------------------
@@ -237,6 +239,9 @@ struct UpdateArgs {
     const int2 *nbr;   // [n] or nullptr (no deposit)
     Scalars *sc;
 };
+
+// Message returned by mmas_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string &msg);
 
 // ---------------------------------------------------------------------------
 // Host launchers (return the launch's cudaError_t)

@@ -331,6 +331,8 @@ mmas_status check_handle(mmas_handle *h)
 
 }  // namespace
 
+void mmas::set_thread_error(const std::string &msg) { tl_error = msg; }
+
 extern "C" {
 
 void mmas_default_params(mmas_params *p)

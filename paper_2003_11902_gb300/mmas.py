@@ -28,7 +28,8 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
-           "mmas_phase_times"]
+           "mmas_phase_times", "mmas_score_tours_noalloc"]
+MMAS_NOALLOC_MAX_ANTS = 1048576
 
 
 class mmas_instance(C.Structure):
@@ -90,6 +91,8 @@ def load(path: str = LIB_PATH):
             "mmas_synchronize": (C.c_int, [H]),
             "mmas_enable_phase_timing": (C.c_int, [H, i32]),
             "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
+            "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
+                                                  C.c_void_p, C.c_void_p, C.c_void_p]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -239,6 +242,18 @@ def mmas_phase_times(h):
     a, b, c = C.c_float(), C.c_float(), C.c_float()
     _check(h, load().mmas_phase_times(h, C.byref(a), C.byref(b), C.byref(c)))
     return a.value, b.value, c.value
+
+
+def mmas_score_tours_noalloc(d_tours: int, m: int, n: int, pitch: int, d_xy: int, d_lens: int,
+                             d_best: int, stream=None):
+    """Allocation-free scoring of m device-resident tours (device addresses as
+    ints, e.g. from torch's data_ptr()): lengths into d_lens, {shortest length,
+    its lowest ant} into d_best.  Asynchronous on ``stream`` (a cudaStream_t
+    value; None uses PyTorch's current stream when available)."""
+    if stream is None:
+        stream = _torch_stream()
+    _check(None, load().mmas_score_tours_noalloc(d_tours, m, n, pitch, d_xy, d_lens, d_best,
+                                                  stream))
 
 
 # ------------------------------------------------------------------- Colony
