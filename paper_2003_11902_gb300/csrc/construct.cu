@@ -255,10 +255,10 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
     const int tb32 = (4 * g) & 31;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (j == 0) philox_rounds<0, 4>(nx, a.key0, a.key1);
-        if (j == 1) philox_rounds<4, 8>(nx, a.key0, a.key1);
+        if (j == 0) philox_rounds_rk<0, 4>(nx, a.rk0, a.rk1);
+        if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
         if (j == 2) {
-            philox_rounds<8, 10>(nx, a.key0, a.key1);
+            philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
             nl[0] = log2f(unit_open(nx.x));
             nl[1] = log2f(unit_open(nx.y));
         }

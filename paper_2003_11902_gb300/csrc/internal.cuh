@@ -63,9 +63,24 @@ __device__ __forceinline__ void philox_rounds(uint4 &c, uint32_t k0, uint32_t k1
     for (int r = R0; r < R1; ++r) {
         const uint32_t rk0 = k0 + (uint32_t)r * 0x9E3779B9u;
         const uint32_t rk1 = k1 + (uint32_t)r * 0xBB67AE85u;
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ rk0, lo1, hi0 ^ c.w ^ rk1, lo0);
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;  // one wide multiply
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0, (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1, (uint32_t)p0);
+    }
+}
+
+// The same rounds with the per-round keys precomputed (rk0[r] = k0 + r W0,
+// rk1[r] = k1 + r W1), e.g. held in kernel parameters.
+template <int R0, int R1>
+__device__ __forceinline__ void philox_rounds_rk(uint4 &c, const uint32_t *rk0, const uint32_t *rk1)
+{
+#pragma unroll
+    for (int r = R0; r < R1; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk1[r], (uint32_t)p0);
     }
 }
 
@@ -188,6 +203,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 struct ConstructArgs {
     int32_t n, m, cl, ld, fallback;
     uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];  // Philox round keys: key + r * Weyl increment
     const int32_t *iter;       // device iteration index
     const uint16_t *cand16;    // [n][cl] candidate ids
     const float *cwinv;        // [n][cl] 1 / choice_info of each candidate

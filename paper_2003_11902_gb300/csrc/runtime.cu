@@ -288,6 +288,10 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.n = n; ca.m = m; ca.cl = cl; ca.ld = ld; ca.fallback = h->p.fallback;
     ca.key0 = (uint32_t)(h->p.seed & 0xFFFFFFFFull);
     ca.key1 = (uint32_t)(h->p.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        ca.rk0[r] = ca.key0 + (uint32_t)r * 0x9E3779B9u;
+        ca.rk1[r] = ca.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     ca.iter = &h->sc->iter;
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
     ca.tours = h->tours; ca.sc = h->sc;
