@@ -75,10 +75,14 @@ typedef struct {
  *            0: take the unvisited node of largest choice_info (ties -> lower id);
  *            1: reservoir-sample all unvisited nodes                (0)
  *   device   CUDA device ordinal                                   (0)
+ *   ant_offset  global index of this colony's first ant: a colony sharded
+ *            over ranks gives each rank ants [ant_offset, ant_offset + m) of
+ *            the whole colony, and the draws are keyed by the global index, so
+ *            the union of the shards builds the same tours as one colony (0)
  *   stream   cudaStream_t to enqueue on, or NULL for a private non-blocking
  *            stream; pass cudaStreamLegacy to use the legacy default stream (NULL)
  *
- * Random draws: start node of ant k in iteration it = word 0 of
+ * Random draws (k = ant_offset + local ant index): start node of ant k in iteration it = word 0 of
  * Philox(ctr = (0xFFFFFFFF, 0, k, it)); candidate slot s at step t = word
  * (t mod 4) of Philox(ctr = (s, t/4, k, it)); whole-row node v at step t =
  * word (v mod 4) of Philox(ctr = (2^31 | v/4, t, k, it)); key = (seed_lo,
@@ -94,6 +98,7 @@ typedef struct {
     int32_t deposit;
     int32_t fallback;
     int32_t device;
+    int32_t ant_offset;
     void *stream;
 } mmas_params;
 

@@ -85,6 +85,7 @@ def lib():
                 "orc_step_keys": (i32, [vp, i32, i32, i32, i32, P(C.c_uint8), P(f64)]),
                 "orc_colony_construct": (i64, [vp, i32, i32, P(i32), P(i64)]),
                 "orc_colony_iterate": (None, [vp, i32]),
+                "orc_colony_update": (None, [vp, P(i32), i64]),
                 "orc_colony_iter": (i32, [vp]),
                 "orc_colony_nn_len": (i64, [vp]),
                 "orc_colony_best": (i64, [vp, P(i32)]),
@@ -272,6 +273,11 @@ class Colony:
     def iterate(self, k: int = 1, threads: int = 1):
         for _ in range(k):
             lib().orc_colony_iterate(self._h, threads)
+
+    def update(self, ib_tour, ib_len):
+        """Alg. 1 after construction, with a given iteration-best tour."""
+        t = np.ascontiguousarray(ib_tour, dtype=np.int32)
+        lib().orc_colony_update(self._h, _i32p(t), int(ib_len))
 
     def best(self):
         tour = np.zeros(self.n, dtype=np.int32)

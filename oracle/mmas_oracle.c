@@ -475,6 +475,28 @@ ORC_API int64_t orc_colony_construct(const orc_colony *c, int32_t it, int32_t an
     return orc_tour_length(n, c->d, tour);
 }
 
+/* The part of Alg. 1's main loop after construction, given the iteration best
+ * tour `ib_tour` of length `ib_len`: global best and trail limits (replaced
+ * only by a strictly shorter tour), evaporation with the new limits, the
+ * deposit on the iteration best (or the global best), choice_info, and the
+ * iteration count. */
+ORC_API void orc_colony_update(orc_colony *c, const int32_t *ib_tour, int64_t ib_len)
+{
+    int32_t n = c->n;
+    if (!c->has_best || ib_len < c->best_len) {
+        memcpy(c->best_tour, ib_tour, sizeof(int32_t) * (size_t)n);
+        c->best_len = ib_len;
+        c->has_best = 1;
+        orc_limits(n, c->rho, c->p_best, c->best_len, &c->tmax, &c->tmin);
+    }
+    orc_evaporate(n, c->tau, c->persist, c->tmin, c->tmax);
+    const int32_t *dep = c->deposit == 0 ? ib_tour : c->best_tour;
+    int64_t dep_len = c->deposit == 0 ? ib_len : c->best_len;
+    orc_deposit(n, c->tau, dep, (float)(1.0 / (double)dep_len), c->tmax);
+    orc_choice(n, c->tau, c->eb, c->alpha, c->choice);
+    c->iter += 1;
+}
+
 /* One iteration of Alg. 1's main loop.  Ants are independent given the
  * pheromone, so `threads` > 1 builds them concurrently (same results). */
 ORC_API void orc_colony_iterate(orc_colony *c, int32_t threads)
@@ -489,22 +511,7 @@ ORC_API void orc_colony_iterate(orc_colony *c, int32_t threads)
     int32_t ib = 0;
     for (int32_t k = 1; k < m; ++k)
         if (c->lens[k] < c->lens[ib]) ib = k;
-
-    /* global best and trail limits, replaced only by a strictly shorter tour */
-    if (!c->has_best || c->lens[ib] < c->best_len) {
-        memcpy(c->best_tour, c->tours + (size_t)ib * n, sizeof(int32_t) * (size_t)n);
-        c->best_len = c->lens[ib];
-        c->has_best = 1;
-        orc_limits(n, c->rho, c->p_best, c->best_len, &c->tmax, &c->tmin);
-    }
-
-    /* evaporation with the new limits, then the deposit on the chosen tour */
-    orc_evaporate(n, c->tau, c->persist, c->tmin, c->tmax);
-    const int32_t *dep = c->deposit == 0 ? c->tours + (size_t)ib * n : c->best_tour;
-    int64_t dep_len = c->deposit == 0 ? c->lens[ib] : c->best_len;
-    orc_deposit(n, c->tau, dep, (float)(1.0 / (double)dep_len), c->tmax);
-    orc_choice(n, c->tau, c->eb, c->alpha, c->choice);
-    c->iter += 1;
+    orc_colony_update(c, c->tours + (size_t)ib * n, c->lens[ib]);
 }
 
 /* ---- accessors (copies out of the colony) ---- */

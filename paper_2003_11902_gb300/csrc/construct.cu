@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     if constexpr (!REGMASK) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
 
     const int stride = gridDim.x * cons_warps;
-    for (int ant = blockIdx.x * cons_warps + warp; ant < a.m; ant += stride) {
+    for (int lant = blockIdx.x * cons_warps + warp; lant < a.m; lant += stride) {
+        const int ant = lant + a.ant_offset;  // global index: keys the draws
         // Alg. 1: the first node is drawn uniformly
         uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
         philox_rounds<0, 10>(s4, a.key0, a.key1);
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
         int cur = start;
         int twin = start;  // lane l holds entry 32w + l of the current window
         uint32_t fbn = 0;
-        int32_t *trow = a.tours + (size_t)ant * a.ld;
+        int32_t *trow = a.tours + (size_t)lant * a.ld;
 
         if constexpr (MODE == CAND) {
             float lg[4];

@@ -202,6 +202,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 // ---------------------------------------------------------------------------
 struct ConstructArgs {
     int32_t n, m, cl, ld, fallback;
+    int32_t ant_offset;        // global index of ant 0 (keys the draws)
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];  // Philox round keys: key + r * Weyl increment
     const int32_t *iter;       // device iteration index

@@ -154,6 +154,8 @@ mmas_status validate(const mmas_instance *inst, const mmas_params *p)
     if (p->deposit != 0 && p->deposit != 1) return fail(nullptr, MMAS_EINVAL, "deposit must be 0 or 1");
     if (p->fallback != 0 && p->fallback != 1)
         return fail(nullptr, MMAS_EINVAL, "fallback must be 0 or 1");
+    if (p->ant_offset < 0 || (long long)p->ant_offset + p->m > INT_MAX)
+        return fail(nullptr, MMAS_EINVAL, "ant_offset must be >= 0 and ant_offset + m < 2^31");
     if (inst->xy) {
         for (int i = 0; i < 2 * n; ++i) {
             const long long c = inst->xy[i];
@@ -286,6 +288,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     // launch arguments of one iteration
     ConstructArgs &ca = h->cargs;
     ca.n = n; ca.m = m; ca.cl = cl; ca.ld = ld; ca.fallback = h->p.fallback;
+    ca.ant_offset = h->p.ant_offset;
     ca.key0 = (uint32_t)(h->p.seed & 0xFFFFFFFFull);
     ca.key1 = (uint32_t)(h->p.seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -352,6 +355,7 @@ void mmas_default_params(mmas_params *p)
     p->deposit = 0;
     p->fallback = 0;
     p->device = 0;
+    p->ant_offset = 0;
     p->stream = nullptr;
 }
 
