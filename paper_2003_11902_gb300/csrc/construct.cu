@@ -321,8 +321,12 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     if constexpr (!REGMASK) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
 
     const int stride = gridDim.x * cons_warps;
-    for (int lant = blockIdx.x * cons_warps + warp; lant < a.m; lant += stride) {
-        const int ant = lant + a.ant_offset;  // global index: keys the draws
+    // `ant` is the global ant index (it keys the draws); this colony's tour rows
+    // start at ant_offset, so the row pointer is taken from a base shifted back
+    // by ant_offset rows (one induction variable keeps the step loop lean)
+    const int ant_end = a.ant_offset + a.m;
+    int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
+    for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride) {
         // Alg. 1: the first node is drawn uniformly
         uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
         philox_rounds<0, 10>(s4, a.key0, a.key1);
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
         int cur = start;
         int twin = start;  // lane l holds entry 32w + l of the current window
         uint32_t fbn = 0;
-        int32_t *trow = a.tours + (size_t)lant * a.ld;
+        int32_t *trow = tours_g + (size_t)ant * a.ld;
 
         if constexpr (MODE == CAND) {
             float lg[4];
