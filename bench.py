@@ -235,6 +235,36 @@ def algorithmic_construct_bytes(w):
     return m * per_ant
 
 
+def time_to_gap(w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=4000):
+    """Wall time from mmas_create until the colony's global best is within `gap`
+    of the oracle's long-run best L* (tests/golden), checking every few
+    iterations (each check reads the best length back to the host)."""
+    from paper_2003_11902_gb300 import Colony
+    path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
+    if w["n"] != 1000 or w["cl"] != 32 or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        lstar = json.load(f)["lstar"]
+    target = (1.0 + gap) * lstar
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, stream=stream, **PARAMS)
+    it, best = 0, None
+    while it < max_iters:
+        col.iterate(check_every)
+        it += check_every
+        best = col.stats()["best_len"]
+        if best <= target:
+            break
+    el = time.perf_counter() - t0
+    col.close()
+    return {"seconds": el if best <= target else None, "iterations": it, "best_len": best,
+            "lstar": lstar, "target": target, "seed": seed,
+            "timed": f"mmas_create + iterations + a best-length read every {check_every} iterations",
+            "lstar_source": "tests/golden/lstar_uniform_n1000.json (oracle, seeds 1-3, 1000 iterations)"}
+
+
 def run_ours(args, w):
     import torch
     import torch.distributed as dist
@@ -336,6 +366,9 @@ def run_ours(args, w):
             "paper_context": "V100, pr1002, cl=32, MMAS-WRS-BT: 0.93 ms construction "
                              "(~1.08M tours/s), Table 6",
         }
+        gapres = time_to_gap(w, xy, seed, dev, stream.cuda_stream)
+        if gapres is not None:
+            line["time_to_2pct_gap"] = gapres
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, xy)
         print(json.dumps(line), flush=True)
