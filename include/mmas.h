@@ -79,6 +79,12 @@ typedef struct {
  *            over ranks gives each rank ants [ant_offset, ant_offset + m) of
  *            the whole colony, and the draws are keyed by the global index, so
  *            the union of the shards builds the same tours as one colony (0)
+ *   ls       local search after construction (Sec. 5.7): 0 none; 1 2-opt the
+ *            iteration best; 2 2-opt every ant's tour.  Bentley's 2-opt with
+ *            the candidate lists as neighbour lists and don't-look bits, first
+ *            improvement, cities visited in index order, runs repeated until
+ *            one makes no move.  Needs cl >= 1 and 9n bytes of shared memory
+ *            per CTA (n <= 24,000 on GB300)                          (0)
  *   stream   cudaStream_t to enqueue on, or NULL for a private non-blocking
  *            stream; pass cudaStreamLegacy to use the legacy default stream (NULL)
  *
@@ -99,6 +105,7 @@ typedef struct {
     int32_t fallback;
     int32_t device;
     int32_t ant_offset;
+    int32_t ls;
     void *stream;
 } mmas_params;
 

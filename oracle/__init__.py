@@ -80,7 +80,7 @@ def lib():
                 "orc_wrs_pick": (i32, [i32, P(i32), P(f64), P(f64)]),
                 "orc_rwm_pick": (i32, [i32, P(f64), f64]),
                 "orc_colony_new": (vp, [i32, P(i32), P(i32), i32, i32, f64, f64, f32, f64, u64,
-                                        i32, i32]),
+                                        i32, i32, i32]),
                 "orc_colony_free": (None, [vp]),
                 "orc_step_keys": (i32, [vp, i32, i32, i32, i32, P(C.c_uint8), P(f64)]),
                 "orc_colony_construct": (i64, [vp, i32, i32, P(i32), P(i64)]),
@@ -93,6 +93,7 @@ def lib():
                 "orc_colony_get": (None, [vp, P(i32), P(f32), P(i32), P(f32), P(f32)]),
                 "orc_colony_tours": (None, [vp, P(i32), P(i64), P(i64)]),
                 "orc_brute_force": (i64, [i32, P(i32), P(i32)]),
+                "orc_two_opt": (i64, [i32, P(i32), P(i32), i32, P(i32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -225,6 +226,16 @@ def rwm_pick(w, u) -> int:
     return lib().orc_rwm_pick(len(w), _f64p(w), float(u))
 
 
+def two_opt(d, nn, tour):
+    """2-opt with neighbour lists nn (n x k) and don't-look bits; returns
+    (improved tour, number of moves)."""
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    nn = np.ascontiguousarray(nn, dtype=np.int32)
+    t = np.array(tour, dtype=np.int32, copy=True, order="C")
+    moves = lib().orc_two_opt(d.shape[0], _i32p(d), _i32p(nn), nn.shape[1], _i32p(t))
+    return t, moves
+
+
 def brute_force(d):
     d = np.ascontiguousarray(d, dtype=np.int32)
     n = d.shape[0]
@@ -239,7 +250,7 @@ class Colony:
     """The oracle's MMAS (Alg. 1) on one instance; same parameters as the C ABI."""
 
     def __init__(self, n=None, xy=None, dist=None, m=1, cl=0, alpha=1.0, beta=2.0, rho=0.02,
-                 p_best=0.01, seed=1, deposit=0, fallback=0):
+                 p_best=0.01, seed=1, deposit=0, fallback=0, ls=0):
         if (xy is None) == (dist is None):
             raise ValueError("give exactly one of xy and dist")
         if xy is not None:
@@ -252,9 +263,12 @@ class Colony:
             xyp, dp = None, _i32p(self._dist)
         self.n, self.m, self.cl = n, m, cl
         self.seed, self.fallback, self.deposit = seed, fallback, deposit
+        if ls and cl < 1:
+            raise ValueError("local search uses the candidate lists: cl must be >= 1")
+        self.ls = ls
         self._h = lib().orc_colony_new(n, xyp, dp, m, cl, float(alpha), float(beta),
                                        float(np.float32(rho)), float(p_best), int(seed),
-                                       deposit, fallback)
+                                       deposit, fallback, ls)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -327,12 +327,15 @@ ORC_API int32_t orc_rwm_pick(int32_t k, const double *w, double u)
     return k - 1;
 }
 
+ORC_API int64_t orc_two_opt(int32_t n, const int32_t *d, const int32_t *nn, int32_t k,
+                            int32_t *tour);
+
 /* ------------------------------------------------------------------------ */
 /* The colony: Alg. 1                                                       */
 /* ------------------------------------------------------------------------ */
 
 typedef struct orc_colony {
-    int32_t n, m, cl, deposit, fallback;
+    int32_t n, m, cl, deposit, fallback, ls;
     double alpha, beta, rho, p_best;
     float persist;
     uint64_t seed;
@@ -358,11 +361,11 @@ typedef struct orc_colony {
 ORC_API orc_colony *orc_colony_new(int32_t n, const int32_t *xy, const int32_t *dist, int32_t m,
                                    int32_t cl, double alpha, double beta, float rho,
                                    double p_best, uint64_t seed, int32_t deposit,
-                                   int32_t fallback)
+                                   int32_t fallback, int32_t ls)
 {
     orc_colony *c = (orc_colony *)calloc(1, sizeof(orc_colony));
     size_t nn = (size_t)n * n;
-    c->n = n; c->m = m; c->cl = cl; c->deposit = deposit; c->fallback = fallback;
+    c->n = n; c->m = m; c->cl = cl; c->deposit = deposit; c->fallback = fallback; c->ls = ls;
     c->alpha = alpha; c->beta = beta; c->rho = (double)rho; c->p_best = p_best;
     c->persist = (float)(1.0 - (double)rho);
     c->seed = seed;
@@ -498,19 +501,32 @@ ORC_API void orc_colony_update(orc_colony *c, const int32_t *ib_tour, int64_t ib
 }
 
 /* One iteration of Alg. 1's main loop.  Ants are independent given the
- * pheromone, so `threads` > 1 builds them concurrently (same results). */
+ * pheromone, so `threads` > 1 builds them concurrently (same results).
+ * Local search (Sec. 5.7), with the candidate lists as neighbour lists:
+ * ls = 1 improves the iteration best with 2-opt, ls = 2 every ant's tour. */
 ORC_API void orc_colony_iterate(orc_colony *c, int32_t threads)
 {
     int32_t n = c->n, m = c->m, it = c->iter;
     (void)threads;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(threads > 0 ? threads : 1)
-    for (int32_t k = 0; k < m; ++k)
-        c->lens[k] = orc_colony_construct(c, it, k, c->tours + (size_t)k * n, &c->fb[k]);
+    for (int32_t k = 0; k < m; ++k) {
+        int32_t *t = c->tours + (size_t)k * n;
+        c->lens[k] = orc_colony_construct(c, it, k, t, &c->fb[k]);
+        if (c->ls == 2) {
+            orc_two_opt(n, c->d, c->cand, c->cl, t);
+            c->lens[k] = orc_tour_length(n, c->d, t);
+        }
+    }
 
     /* iteration best: shortest tour, ties -> lower ant index */
     int32_t ib = 0;
     for (int32_t k = 1; k < m; ++k)
         if (c->lens[k] < c->lens[ib]) ib = k;
+    if (c->ls == 1) {
+        int32_t *t = c->tours + (size_t)ib * n;
+        orc_two_opt(n, c->d, c->cand, c->cl, t);
+        c->lens[ib] = orc_tour_length(n, c->d, t);
+    }
     orc_colony_update(c, c->tours + (size_t)ib * n, c->lens[ib]);
 }
 
@@ -542,6 +558,117 @@ ORC_API void orc_colony_tours(const orc_colony *c, int32_t *tours, int64_t *lens
     if (tours) memcpy(tours, c->tours, sizeof(int32_t) * (size_t)c->m * c->n);
     if (lens) memcpy(lens, c->lens, sizeof(int64_t) * (size_t)c->m);
     if (fb) memcpy(fb, c->fb, sizeof(int64_t) * (size_t)c->m);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 2-opt local search (Sec. 5.7): Bentley's neighbour-list 2-opt with       */
+/* don't-look bits, first improvement                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Reverse the tour between positions a and b inclusive, going forward
+ * (circularly) from a; keeps pos[] the inverse of tour[]. */
+static void reverse_path(int32_t n, int32_t *tour, int32_t *pos, int32_t a, int32_t b)
+{
+    int32_t len = (b - a + n) % n + 1;
+    for (int32_t s = 0; s < len / 2; ++s) {
+        int32_t i = (a + s) % n, j = (b - s + n) % n;
+        int32_t ci = tour[i], cj = tour[j];
+        tour[i] = cj; pos[cj] = i;
+        tour[j] = ci; pos[ci] = j;
+    }
+}
+
+/* Apply the 2-opt move that removes edges (u1, v1) and (u2, v2), where v1
+ * follows u1 and v2 follows u2 in tour order, and adds (u1, u2), (v1, v2):
+ * reverse the path v1..u2, or -- when it is longer than half the tour --
+ * the complementary path v2..u1, which gives the same cycle. */
+static void apply_2opt(int32_t n, int32_t *tour, int32_t *pos, int32_t u1, int32_t v1, int32_t u2,
+                       int32_t v2)
+{
+    int32_t a = pos[v1], b = pos[u2];
+    int32_t len = (b - a + n) % n + 1;
+    if (2 * len <= n) reverse_path(n, tour, pos, a, b);
+    else reverse_path(n, tour, pos, pos[v2], pos[u1]);
+}
+
+/* The first improving 2-opt move at city c1 (Bentley 1992, as Sec. 5.7 says):
+ * first with c1's successor s1, over c1's neighbours c2 in list order while
+ * d(c1,c2) < d(c1,s1): gain d(c1,s1) + d(c2,s2) - d(c1,c2) - d(s1,s2), s2 the
+ * successor of c2; then the same with predecessors.  Returns 1 and the move's
+ * four cities (u1 -> v1 and u2 -> v2 are the removed edges in tour order), or
+ * 0 when there is none. */
+static int find_2opt(int32_t n, const int32_t *d, const int32_t *nn, int32_t k,
+                     const int32_t *tour, const int32_t *pos, int32_t c1, int32_t mv[4])
+{
+    int32_t p = pos[c1];
+    int32_t s1 = tour[(p + 1) % n], p1 = tour[(p - 1 + n) % n];
+    int32_t radius = d[(size_t)c1 * n + s1];
+    for (int32_t h = 0; h < k; ++h) {
+        int32_t c2 = nn[(size_t)c1 * k + h];
+        int32_t d12 = d[(size_t)c1 * n + c2];
+        if (d12 >= radius) break;
+        int32_t s2 = tour[(pos[c2] + 1) % n];
+        int64_t gain = (int64_t)radius + d[(size_t)c2 * n + s2] - d12 - d[(size_t)s1 * n + s2];
+        if (gain > 0) {
+            mv[0] = c1; mv[1] = s1; mv[2] = c2; mv[3] = s2;
+            return 1;
+        }
+    }
+    radius = d[(size_t)p1 * n + c1];
+    for (int32_t h = 0; h < k; ++h) {
+        int32_t c2 = nn[(size_t)c1 * k + h];
+        int32_t d12 = d[(size_t)c1 * n + c2];
+        if (d12 >= radius) break;
+        int32_t p2 = tour[(pos[c2] - 1 + n) % n];
+        int64_t gain = (int64_t)radius + d[(size_t)p2 * n + c2] - d12 - d[(size_t)p1 * n + p2];
+        if (gain > 0) {
+            /* removed edges p1 -> c1 and p2 -> c2 */
+            mv[0] = p2; mv[1] = c2; mv[2] = p1; mv[3] = c1;
+            return 1;
+        }
+    }
+    return 0;
+}
+
+/* 2-opt to a local optimum of the neighbour-list neighbourhood.  A run starts
+ * with every don't-look bit clear and makes passes over the cities in index
+ * order, skipping cities whose bit is set; a city without a move gets its bit
+ * set, a move clears the bits of its four cities; the run ends after a pass
+ * without a move.  Don't-look bits can hide a move that appeared after a
+ * city's bit was set, so runs repeat until a whole run makes no move.
+ * Returns the number of moves; the tour is improved in place. */
+ORC_API int64_t orc_two_opt(int32_t n, const int32_t *d, const int32_t *nn, int32_t k,
+                            int32_t *tour)
+{
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint8_t *dlb = (uint8_t *)malloc((size_t)n);
+    for (int32_t i = 0; i < n; ++i) pos[tour[i]] = i;
+    int64_t moves = 0;
+    for (;;) {
+        memset(dlb, 0, (size_t)n);
+        int64_t run_moves = 0;
+        int improved = 1;
+        while (improved) {
+            improved = 0;
+            for (int32_t c1 = 0; c1 < n; ++c1) {
+                if (dlb[c1]) continue;
+                int32_t mv[4];
+                if (find_2opt(n, d, nn, k, tour, pos, c1, mv)) {
+                    apply_2opt(n, tour, pos, mv[0], mv[1], mv[2], mv[3]);
+                    for (int q = 0; q < 4; ++q) dlb[mv[q]] = 0;
+                    improved = 1;
+                    ++run_moves;
+                } else {
+                    dlb[c1] = 1;
+                }
+            }
+        }
+        moves += run_moves;
+        if (run_moves == 0) break;
+    }
+    free(pos);
+    free(dlb);
+    return moves;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -50,6 +50,7 @@ struct mmas_handle {
     ConstructPlan cplan{};
     BestArgs bargs{};
     ScoreArgs sargs{};
+    TwoOptArgs targs{};
     UpdateArgs uargs{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -129,6 +130,8 @@ mmas_status sync_and_check(mmas_handle *h)
         cudaMemcpy(&h->sc->err, &zero, sizeof(zero), cudaMemcpyHostToDevice);
         if (e & ERR_STAGE_TIMEOUT)
             return fail(h, MMAS_ETIMEOUT, "a shared-memory staging wait on the device timed out");
+        if (e & ERR_LS_CAP)
+            return fail(h, MMAS_ESTATE, "a 2-opt search exceeded its move cap and stopped early");
         return fail(h, MMAS_ESTATE, "the device found no unvisited node during a selection");
     }
     return MMAS_OK;
@@ -156,6 +159,9 @@ mmas_status validate(const mmas_instance *inst, const mmas_params *p)
         return fail(nullptr, MMAS_EINVAL, "fallback must be 0 or 1");
     if (p->ant_offset < 0 || (long long)p->ant_offset + p->m > INT_MAX)
         return fail(nullptr, MMAS_EINVAL, "ant_offset must be >= 0 and ant_offset + m < 2^31");
+    if (p->ls < 0 || p->ls > 2) return fail(nullptr, MMAS_EINVAL, "ls must be 0, 1 or 2");
+    if (p->ls > 0 && p->cl < 1)
+        return fail(nullptr, MMAS_EINVAL, "ls needs candidate lists (cl >= 1) as neighbour lists");
     if (inst->xy) {
         for (int i = 0; i < 2 * n; ++i) {
             const long long c = inst->xy[i];
@@ -186,7 +192,17 @@ mmas_status capture_iteration(mmas_handle *h)
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[0], cs, cudaEventRecordExternal);
     if (e == cudaSuccess) e = launch_construct(h->cargs, h->cplan, cs);
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[1], cs, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_score(h->sargs, h->num_sms, cs);
+    if (h->p.ls == 1) {
+        // lengths, 2-opt of the iteration best, then best / limits
+        ScoreArgs sa = h->sargs;
+        sa.best = 0;
+        if (e == cudaSuccess) e = launch_score(sa, h->num_sms, cs);
+        if (e == cudaSuccess) e = launch_two_opt(h->targs, true, h->num_sms, cs);
+        if (e == cudaSuccess) e = launch_best(h->bargs, cs);
+    } else {
+        if (h->p.ls == 2 && e == cudaSuccess) e = launch_two_opt(h->targs, false, h->num_sms, cs);
+        if (e == cudaSuccess) e = launch_score(h->sargs, h->num_sms, cs);
+    }
     if (e == cudaSuccess) e = launch_update(h->uargs, h->num_sms, cs);
     if (e == cudaSuccess && h->timing) e = cudaEventRecordWithFlags(h->ev[2], cs, cudaEventRecordExternal);
     cudaGraph_t g = nullptr;
@@ -312,6 +328,13 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     sa.n = n; sa.m = m; sa.ld = ld; sa.best = 1;
     sa.tours = h->tours; sa.xy = h->xy; sa.dist = h->dist; sa.lens = h->lens; sa.b = ba;
 
+    TwoOptArgs &ta = h->targs;
+    ta.n = n; ta.m = m; ta.ld = ld; ta.k = cl;
+    ta.nn = h->cand32; ta.xy = h->xy; ta.dist = h->dist; ta.tours = h->tours; ta.lens = h->lens;
+    ta.err = &h->sc->err;
+    if (h->p.ls > 0 && two_opt_smem(n) > h->smem_optin)
+        return fail(h, MMAS_EINVAL, "ls needs 9n bytes of shared memory per CTA: n is too large");
+
     UpdateArgs &ua = h->uargs;
     ua.n = n; ua.ld = ld; ua.cl = cl; ua.fullrow = cl == 0; ua.evaporate = 1;
     ua.persist = (float)(1.0 - (double)h->p.rho);
@@ -356,6 +379,7 @@ void mmas_default_params(mmas_params *p)
     p->fallback = 0;
     p->device = 0;
     p->ant_offset = 0;
+    p->ls = 0;
     p->stream = nullptr;
 }
 

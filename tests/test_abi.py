@@ -33,9 +33,9 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layout_matches_header():
-    assert C.sizeof(mmas.mmas_params) == 56
+    assert C.sizeof(mmas.mmas_params) == 64
     assert mmas.mmas_params.seed.offset == 24
-    assert mmas.mmas_params.stream.offset == 48
+    assert mmas.mmas_params.stream.offset == 56
     assert C.sizeof(mmas.mmas_instance) == 24
 
 
@@ -48,7 +48,7 @@ def test_default_params(lib):
 @pytest.mark.parametrize("field,value,needle", [
     ("rho", 0.0, "rho"), ("rho", 1.0, "rho"), ("p_best", 1.0, "p_best"), ("alpha", -1.0, "alpha"),
     ("beta", float("nan"), "beta"), ("cl", 33, "cl"), ("cl", -1, "cl"), ("m", -5, "m must"),
-    ("deposit", 2, "deposit"), ("fallback", 3, "fallback"),
+    ("deposit", 2, "deposit"), ("fallback", 3, "fallback"), ("ls", 3, "ls"),
 ])
 def test_bad_parameters_are_rejected_before_device_work(lib, field, value, needle):
     p = mmas.mmas_default_params()

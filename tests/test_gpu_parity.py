@@ -24,7 +24,7 @@ def built():
 def _pair(xy=None, dist=None, **kw):
     g = Colony(xy=xy, dist=dist, **kw)
     okw = {k: v for k, v in kw.items() if k in ("m", "cl", "alpha", "beta", "rho", "p_best",
-                                                 "seed", "deposit", "fallback")}
+                                                 "seed", "deposit", "fallback", "ls")}
     for k in ("alpha", "beta", "p_best"):
         if k in okw:
             okw[k] = float(np.float32(okw[k]))
@@ -337,3 +337,32 @@ def test_phase_timing_is_a_pure_measurement():
         a.phase_times()
     a.close()
     b.close()
+
+
+# ------------------------------------------------------------------ 2-opt local search
+
+@pytest.mark.parametrize("kind,n,m,cl,ls,iters", [
+    ("uniform", 50, 20, 8, 2, 3),        # every ant, 256-city windows
+    ("uniform", 1000, 48, 32, 2, 1),     # every ant at the n = 1000 size
+    ("uniform", 300, 40, 16, 1, 5),      # the iteration best, 1024-city windows
+    ("clustered", 3800, 64, 16, 1, 1),   # the clustered n = 3800 shape, iteration best
+])
+def test_two_opt_matches_oracle(kind, n, m, cl, ls, iters):
+    xy = I.uniform(n, 400 + n) if kind == "uniform" else I.clustered(n, 3)
+    g, o = _pair(xy=xy, m=m, cl=cl, rho=0.1, seed=6, ls=ls)
+    for it in range(iters):
+        g.iterate(1)
+        o.iterate(1)
+        tours, lens = g.tours()
+        otours, olens, _ = o.tours()
+        assert np.array_equal(lens, olens), f"iteration {it}: lengths differ"
+        assert np.array_equal(tours, otours), f"iteration {it}: tours differ"
+        assert g.best_tour()[0] == o.best()[0]
+    tau, tmin, tmax = g.pheromone()
+    np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
+    g.close()
+
+
+def test_two_opt_needs_candidate_lists():
+    with pytest.raises(MMASError, match="ls needs"):
+        Colony(xy=I.uniform(30, 1), cl=0, ls=1)
