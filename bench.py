@@ -45,8 +45,13 @@ WORKLOADS = {
     # name: (n, m, cl, instance kind, instance seed)
     "uniform-n1000-cl32": dict(n=1000, m=1000, cl=32, kind="uniform", iseed=1001),
     "uniform-n200-fullrow": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002),
+    "clustered-n3800-cl16-2opt": dict(n=3800, m=1000, cl=16, kind="clustered", iseed=1003, ls=1),
 }
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
+# kernels in one iteration graph: construct, score, update; with 2-opt of the
+# iteration best also the 2-opt and the best/limits kernel; with 2-opt of every
+# ant the 2-opt kernel before scoring
+KERNELS_PER_ITERATION = {0: 3, 1: 5, 2: 4}
 METRIC = "candidate tours/sec (one MMAS iteration per step)"
 UNIT = "tours/s"
 FLUSH_BYTES = 256 << 20
@@ -151,7 +156,7 @@ def cpu_baseline(w, xy, budget_s=12.0):
     """The oracle as it stands, all host cores, whole iterations until budget_s."""
     import oracle as O
     cores = os.cpu_count() or 1
-    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, **PARAMS)
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **PARAMS)
     it, t0 = 0, time.perf_counter()
     while True:
         col.iterate(1, threads=cores)
@@ -172,7 +177,7 @@ def run_reference(args, w):
     import oracle as O
     xy = _instance(w)
     cores = os.cpu_count() or 1
-    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, **PARAMS)
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **PARAMS)
     t0 = time.perf_counter()
     col.iterate(1, threads=cores)
     t_iter = time.perf_counter() - t0
@@ -219,8 +224,11 @@ def run_reference(args, w):
 
 
 def _cfg(w):
-    return {"n": w["n"], "m": w["m"], "cl": w["cl"], "instance": f"{w['kind']} seed {w['iseed']}",
-            **PARAMS}
+    c = {"n": w["n"], "m": w["m"], "cl": w["cl"], "instance": f"{w['kind']} seed {w['iseed']}",
+         **PARAMS}
+    if w.get("ls"):
+        c["local_search"] = "2-opt of the iteration best" if w["ls"] == 1 else "2-opt of every ant"
+    return c
 
 
 def algorithmic_construct_bytes(w):
@@ -281,7 +289,7 @@ def run_ours(args, w):
     seed = 1 + rank
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)  # the flush, the colony and all timing share this stream
-    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev,
+    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, ls=w.get("ls", 0),
                  stream=stream.cuda_stream, **PARAMS)
     col.enable_phase_timing(True)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -318,8 +326,8 @@ def run_ours(args, w):
     # end to end through the C ABI with host buffers
     e2e_total = 0.0
     t0 = time.perf_counter()
-    col2 = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, stream=stream.cuda_stream,
-                  **PARAMS)
+    col2 = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, ls=w.get("ls", 0),
+                  stream=stream.cuda_stream, **PARAMS)
     col2.synchronize()
     e2e_total += time.perf_counter() - t0
     for _ in range(args.steps):
@@ -359,7 +367,7 @@ def run_ours(args, w):
                          "algorithmic_bytes_per_launch": algo},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["n"] / args.steps,
                     "d2h_bytes_per_step": 4 * w["n"] + 64},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": KERNELS_PER_ITERATION[w.get("ls", 0)] * args.steps,
             "clocks": clocks,
             "best_len": best_len, "fallback_steps": st["fallback_steps"],
             "wall_s": wall,

@@ -83,8 +83,8 @@ typedef struct {
  *            iteration best; 2 2-opt every ant's tour.  Bentley's 2-opt with
  *            the candidate lists as neighbour lists and don't-look bits, first
  *            improvement, cities visited in index order, runs repeated until
- *            one makes no move.  Needs cl >= 1 and 9n bytes of shared memory
- *            per CTA (n <= 24,000 on GB300)                          (0)
+ *            one makes no move.  Needs cl >= 1 and 13n bytes of shared memory
+ *            per CTA (n <= 17,800 on GB300)                          (0)
  *   stream   cudaStream_t to enqueue on, or NULL for a private non-blocking
  *            stream; pass cudaStreamLegacy to use the legacy default stream (NULL)
  *

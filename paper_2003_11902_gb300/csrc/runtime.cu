@@ -44,6 +44,7 @@ struct mmas_handle {
     Scalars *sc = nullptr;
     int *maxd = nullptr;
     int32_t *ext_tour = nullptr, *ext_len = nullptr;
+    int32_t *nnd = nullptr;
     Scalars *h_sc = nullptr;  // pinned mirror of *sc
 
     ConstructArgs cargs{};
@@ -104,18 +105,21 @@ void free_all(mmas_handle *h)
         if (e) cudaEventDestroy(e);
     void *bufs[] = {h->xy,      h->dist,   h->eb,      h->tau,     h->wmat, h->cwinv,
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
-                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len};
+                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->nnd};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+// Allocate and zero a device buffer; the zeroing is ordered on `stream`, the
+// stream every later kernel of the handle runs on (a plain cudaMemset would run
+// on the legacy stream, unordered with a non-blocking one).
 template <typename T>
-cudaError_t dalloc(T **p, size_t bytes)
+cudaError_t dalloc(T **p, size_t bytes, cudaStream_t stream)
 {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
-    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes ? bytes : 16);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes ? bytes : 16, stream);
     return e;
 }
 
@@ -252,29 +256,29 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
 
     const size_t cw_bytes = pad16((size_t)n * (cl ? cl : 1) * sizeof(float));
     const size_t cc_bytes = pad16((size_t)n * (cl ? cl : 1) * sizeof(uint16_t));
-    CK(h, dalloc(&h->dist, nn * sizeof(int32_t)));
-    CK(h, dalloc(&h->eb, nn * sizeof(float)));
-    CK(h, dalloc(&h->tau, nn * sizeof(float)));
-    CK(h, dalloc(&h->wmat, nn * sizeof(float)));
-    CK(h, dalloc(&h->cand32, (size_t)n * (cl ? cl : 1) * sizeof(int32_t)));
-    CK(h, dalloc(&h->cand16, cc_bytes));
-    CK(h, dalloc(&h->cwinv, cw_bytes));
-    CK(h, dalloc(&h->tours, (size_t)m * ld * sizeof(int32_t)));
-    CK(h, dalloc(&h->lens, (size_t)m * sizeof(int32_t)));
-    CK(h, dalloc(&h->gb_tour, (size_t)n * sizeof(int32_t)));
-    CK(h, dalloc(&h->nn_tour, (size_t)n * sizeof(int32_t)));
-    CK(h, dalloc(&h->nbr, (size_t)n * sizeof(int2)));
-    CK(h, dalloc(&h->sc, sizeof(Scalars)));
-    CK(h, dalloc(&h->maxd, sizeof(int)));
-    CK(h, dalloc(&h->ext_tour, (size_t)n * sizeof(int32_t)));
-    CK(h, dalloc(&h->ext_len, sizeof(int32_t)));
+    CK(h, dalloc(&h->dist, nn * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->eb, nn * sizeof(float), h->stream));
+    CK(h, dalloc(&h->tau, nn * sizeof(float), h->stream));
+    CK(h, dalloc(&h->wmat, nn * sizeof(float), h->stream));
+    CK(h, dalloc(&h->cand32, (size_t)n * (cl ? cl : 1) * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->cand16, cc_bytes, h->stream));
+    CK(h, dalloc(&h->cwinv, cw_bytes, h->stream));
+    CK(h, dalloc(&h->tours, (size_t)m * ld * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->lens, (size_t)m * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->gb_tour, (size_t)n * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->nn_tour, (size_t)n * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->nbr, (size_t)n * sizeof(int2), h->stream));
+    CK(h, dalloc(&h->sc, sizeof(Scalars), h->stream));
+    CK(h, dalloc(&h->maxd, sizeof(int), h->stream));
+    CK(h, dalloc(&h->ext_tour, (size_t)n * sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->ext_len, sizeof(int32_t), h->stream));
     CK(h, cudaMallocHost(reinterpret_cast<void **>(&h->h_sc), sizeof(Scalars)));
     std::memset(h->h_sc, 0, sizeof(Scalars));
 
     // instance -> device, distances, overflow check
     cudaStream_t s = h->stream;
     if (inst->xy) {
-        CK(h, dalloc(&h->xy, (size_t)n * sizeof(int2)));
+        CK(h, dalloc(&h->xy, (size_t)n * sizeof(int2), h->stream));
         CK(h, cudaMemcpyAsync(h->xy, inst->xy, (size_t)n * sizeof(int2), cudaMemcpyHostToDevice, s));
         CK(h, launch_distances(h->xy, n, ld, h->dist, h->maxd, s));
     } else {
@@ -333,7 +337,12 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ta.nn = h->cand32; ta.xy = h->xy; ta.dist = h->dist; ta.tours = h->tours; ta.lens = h->lens;
     ta.err = &h->sc->err;
     if (h->p.ls > 0 && two_opt_smem(n) > h->smem_optin)
-        return fail(h, MMAS_EINVAL, "ls needs 9n bytes of shared memory per CTA: n is too large");
+        return fail(h, MMAS_EINVAL, "ls needs 13n bytes of shared memory per CTA: n is too large");
+    if (h->p.ls > 0) {
+        CK(h, dalloc(&h->nnd, (size_t)n * cl * sizeof(int32_t), h->stream));
+        CK(h, launch_neighbour_dist(ta, h->nnd, s));
+        ta.nnd = h->nnd;
+    }
 
     UpdateArgs &ua = h->uargs;
     ua.n = n; ua.ld = ld; ua.cl = cl; ua.fullrow = cl == 0; ua.evaporate = 1;

@@ -1,20 +1,24 @@
 // 2-opt local search (Sec. 5.7): Bentley's neighbour-list 2-opt with
 // don't-look bits, first improvement, on whole tours.
 //
-// One CTA improves one tour held in shared memory (tour, position of each
-// city, don't-look bits: 9 bytes per city).  The sequential search visits the
-// cities in index order, skipping those whose don't-look bit is set; a city
+// One CTA improves one tour held in shared memory (tour and position of each
+// city, the length of each tour edge, don't-look bits: 13 bytes per city).
+// The sequential search visits the cities in index order, skipping those
+// whose don't-look bit is set; a city
 // without a move gets its bit set, a move clears the bits of its four cities
 // and the visit continues after the moving city; a run ends after a pass with
 // no move, and runs (from cleared bits) repeat until a run makes no move.
-// Here each round evaluates a window of blockDim consecutive cities in
-// parallel against the current tour and applies the lowest-index improving
-// move; the window's earlier cities had no move, so they get their bits set.
-// That is exactly the sequential search, move for move, for any window size.
-// A move reverses the shorter of the two paths it cuts, with all threads.
+// Here each round evaluates a window of consecutive cities in parallel against
+// the current tour and applies the lowest-index improving move; the window's
+// earlier cities had no move, so they get their bits set.  That is exactly the
+// sequential search, move for move, for any window size: the window is 32
+// cities after a move (moves come densely) and doubles, up to blockDim, while
+// windows find none.  A move reverses the shorter of the two paths it cuts,
+// with all threads.
 //
-// Neighbour lists are the colony's candidate lists.  Distances are the exact
-// integer ones (coordinates or the explicit matrix).
+// Neighbour lists are the colony's candidate lists, with their distances
+// precomputed.  Distances are the exact integer ones (coordinates or the
+// explicit matrix).
 #include <climits>
 
 #include "internal.cuh"
@@ -32,40 +36,50 @@ __device__ __forceinline__ int32_t dij(const TwoOptArgs &a, int u, int v)
         return __ldg(a.dist + (size_t)u * a.ld + v);
 }
 
+// Shared-memory image of one tour: tour[i], pos[c], and
+// edge[i] = d(tour[i], tour[i+1 mod n]) kept exact under every move.
+struct TourView {
+    int32_t *tour, *pos;
+    int32_t *edge;
+    int n;
+    __device__ __forceinline__ int nxt(int i) const { return i + 1 == n ? 0 : i + 1; }
+    __device__ __forceinline__ int prv(int i) const { return i == 0 ? n - 1 : i - 1; }
+};
+
 // First improving move at city c1: successor side, then predecessor side,
 // neighbours in list order while closer than the tour neighbour on that side.
 // mv = {u1, v1, u2, v2}: remove u1->v1 and u2->v2, add u1-u2 and v1-v2.
+// Tour-edge lengths come from the edge array, neighbour distances from the
+// precomputed lists; one distance is computed per neighbour examined.
 template <bool XY>
-__device__ __forceinline__ bool find_move(const TwoOptArgs &a, const int32_t *tour,
-                                          const int32_t *pos, int c1, int mv[4])
+__device__ __forceinline__ bool find_move(const TwoOptArgs &a, const TourView &tv, int c1,
+                                          int mv[4])
 {
-    const int n = a.n;
-    const int p = pos[c1];
-    const int s1 = tour[p + 1 == n ? 0 : p + 1], p1 = tour[p == 0 ? n - 1 : p - 1];
+    const int p = tv.pos[c1];
+    const int s1 = tv.tour[tv.nxt(p)], p1 = tv.tour[tv.prv(p)];
     const int32_t *nn = a.nn + (size_t)c1 * a.k;
-    int radius = dij<XY>(a, c1, s1);
+    const int32_t *dn = a.nnd + (size_t)c1 * a.k;
+    int radius = tv.edge[p];
     for (int h = 0; h < a.k; ++h) {
-        const int c2 = __ldg(nn + h);
-        const int d12 = dij<XY>(a, c1, c2);
+        const int d12 = __ldg(dn + h);
         if (d12 >= radius) break;
-        const int q = pos[c2];
-        const int s2 = tour[q + 1 == n ? 0 : q + 1];
-        const long long gain =
-            (long long)radius + dij<XY>(a, c2, s2) - d12 - dij<XY>(a, s1, s2);
+        const int c2 = __ldg(nn + h);
+        const int q = tv.pos[c2];
+        const int s2 = tv.tour[tv.nxt(q)];
+        const long long gain = (long long)radius + tv.edge[q] - d12 - dij<XY>(a, s1, s2);
         if (gain > 0) {
             mv[0] = c1; mv[1] = s1; mv[2] = c2; mv[3] = s2;
             return true;
         }
     }
-    radius = dij<XY>(a, p1, c1);
+    radius = tv.edge[tv.prv(p)];
     for (int h = 0; h < a.k; ++h) {
-        const int c2 = __ldg(nn + h);
-        const int d12 = dij<XY>(a, c1, c2);
+        const int d12 = __ldg(dn + h);
         if (d12 >= radius) break;
-        const int q = pos[c2];
-        const int p2 = tour[q == 0 ? n - 1 : q - 1];
-        const long long gain =
-            (long long)radius + dij<XY>(a, p2, c2) - d12 - dij<XY>(a, p1, p2);
+        const int c2 = __ldg(nn + h);
+        const int q = tv.pos[c2];
+        const int p2 = tv.tour[tv.prv(q)];
+        const long long gain = (long long)radius + tv.edge[tv.prv(q)] - d12 - dij<XY>(a, p1, p2);
         if (gain > 0) {
             mv[0] = p2; mv[1] = c2; mv[2] = p1; mv[3] = c1;
             return true;
@@ -79,8 +93,12 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
 {
     extern __shared__ __align__(16) int32_t sm[];
     const int n = a.n, tid = threadIdx.x, W = blockDim.x;
-    int32_t *s_tour = sm, *s_pos = sm + n;
-    unsigned char *s_dlb = reinterpret_cast<unsigned char *>(sm + 2 * n);
+    TourView tv;
+    tv.n = n;
+    tv.edge = sm;
+    tv.tour = sm + n;
+    tv.pos = sm + 2 * n;
+    unsigned char *s_dlb = reinterpret_cast<unsigned char *>(tv.pos + n);
     __shared__ int s_first, s_red[32];
     __shared__ unsigned long long s_best;
     __shared__ int s_mv[4];
@@ -109,8 +127,9 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
         int32_t *row = a.tours + (size_t)ti * a.ld;
         for (int i = tid; i < n; i += W) {
             const int c = row[i];
-            s_tour[i] = c;
-            s_pos[c] = i;
+            tv.tour[i] = c;
+            tv.pos[c] = i;
+            tv.edge[i] = dij<XY>(a, c, row[i + 1 == n ? 0 : i + 1]);
         }
         __syncthreads();
         // every move shortens the tour by >= 1, so the search ends; the cap
@@ -126,46 +145,61 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
             while (improved && !capped) {  // passes
                 improved = false;
                 int l = 0;
+                int w = 32;  // window: 32 cities after a move, doubling while none is found
                 while (l < n) {  // windows
                     const int c1 = l + tid;
+                    const bool in = tid < w && c1 < n;
                     int mv[4];
-                    const bool has = c1 < n && !s_dlb[c1] && find_move<XY>(a, s_tour, s_pos, c1, mv);
+                    const bool has = in && !s_dlb[c1] && find_move<XY>(a, tv, c1, mv);
                     if (tid == 0) s_first = INT_MAX;
                     __syncthreads();
                     if (has) atomicMin(&s_first, c1);
                     __syncthreads();
                     const int first = s_first;
                     if (first == INT_MAX) {
-                        if (c1 < n) s_dlb[c1] = 1;
-                        l += W;
+                        if (in) s_dlb[c1] = 1;
+                        l += w;
+                        w = w * 2 < W ? w * 2 : W;
                         __syncthreads();
                         continue;
                     }
-                    if (c1 < first) s_dlb[c1] = 1;  // evaluated, no move
+                    w = 32;
+                    if (in && c1 < first) s_dlb[c1] = 1;  // evaluated, no move
                     if (c1 == first) {
                         s_mv[0] = mv[0]; s_mv[1] = mv[1]; s_mv[2] = mv[2]; s_mv[3] = mv[3];
                     }
                     __syncthreads();
                     const int u1 = s_mv[0], v1 = s_mv[1], u2 = s_mv[2], v2 = s_mv[3];
-                    int pa = s_pos[v1], pb = s_pos[u2];
+                    int pa = tv.pos[v1], pb = tv.pos[u2];
                     int len = (pb - pa + n) % n + 1;
                     if (2 * len > n) {  // reverse the complementary, shorter path
-                        pa = s_pos[v2];
-                        pb = s_pos[u1];
+                        pa = tv.pos[v2];
+                        pb = tv.pos[u1];
                         len = n - len;
                     }
                     __syncthreads();  // every thread has read the positions
-                    for (int s = tid; s < len / 2; s += W) {
-                        const int i = (pa + s) % n, j = (pb - s + n) % n;
-                        const int ci = s_tour[i], cj = s_tour[j];
-                        s_tour[i] = cj;
-                        s_pos[cj] = i;
-                        s_tour[j] = ci;
-                        s_pos[ci] = j;
+                    // reverse tour[pa..pb]; the len-1 edges inside it reverse too
+                    for (int s2 = tid; s2 < len / 2; s2 += W) {
+                        const int i = (pa + s2) % n, j = (pb - s2 + n) % n;
+                        const int ci = tv.tour[i], cj = tv.tour[j];
+                        tv.tour[i] = cj;
+                        tv.pos[cj] = i;
+                        tv.tour[j] = ci;
+                        tv.pos[ci] = j;
+                    }
+                    for (int s2 = tid; s2 < (len - 1) / 2; s2 += W) {
+                        const int i = (pa + s2) % n, j = (pb - 1 - s2 + n) % n;
+                        const int ei = tv.edge[i];
+                        tv.edge[i] = tv.edge[j];
+                        tv.edge[j] = ei;
                     }
                     __syncthreads();
                     if (tid == 0) {
                         s_dlb[u1] = 0; s_dlb[v1] = 0; s_dlb[u2] = 0; s_dlb[v2] = 0;
+                        // the two added edges now border the reversed path
+                        const int ia = tv.prv(pa);
+                        tv.edge[ia] = dij<XY>(a, tv.tour[ia], tv.tour[pa]);
+                        tv.edge[pb] = dij<XY>(a, tv.tour[pb], tv.tour[tv.nxt(pb)]);
                     }
                     improved = true;
                     ++run_moves;
@@ -183,9 +217,8 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
         // write back and measure the improved tour
         int part = 0;
         for (int i = tid; i < n; i += W) {
-            const int u = s_tour[i], v = s_tour[i + 1 == n ? 0 : i + 1];
-            row[i] = u;
-            part += dij<XY>(a, u, v);
+            row[i] = tv.tour[i];
+            part += tv.edge[i];
         }
         part = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)part);
         if ((tid & 31) == 0) s_red[tid >> 5] = part;
@@ -199,9 +232,30 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
     }
 }
 
+// d(c, nn[c][h]) for every city and neighbour (set-up, once).
+template <bool XY>
+__global__ void k_neighbour_dist(const TwoOptArgs a, int32_t *nnd)
+{
+    const size_t total = (size_t)a.n * a.k;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / a.k);
+        nnd[e] = dij<XY>(a, c, a.nn[e]);
+    }
+}
+
 }  // namespace
 
-size_t two_opt_smem(int n) { return (size_t)9 * n + 16; }
+size_t two_opt_smem(int n) { return (size_t)13 * n + 16; }
+
+cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s)
+{
+    if (a.xy)
+        k_neighbour_dist<true><<<256, 256, 0, s>>>(a, nnd);
+    else
+        k_neighbour_dist<false><<<256, 256, 0, s>>>(a, nnd);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, cudaStream_t s)
 {
