@@ -1,6 +1,6 @@
 """Build libmmas.so (sm_103a) in-tree with nvcc.
 
-The four CUDA translation units compile in parallel into ``_build/`` at the
+The CUDA translation units compile in parallel into ``_build/`` at the
 repository root and link into ``paper_2003_11902_gb300/libmmas.so`` with the
 static CUDA runtime.  ``build()`` is a no-op when the library is newer than
 every source and header.
@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SO = os.path.join(HERE, "libmmas.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["setup.cu", "construct.cu", "pheromone.cu", "twoopt.cu", "runtime.cu", "noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "internal.cuh"), os.path.join(INCLUDE, "mmas.h")]
+HEADERS = [os.path.join(CSRC, h) for h in ("internal.cuh", "twoopt.cuh")] + [os.path.join(INCLUDE, "mmas.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -245,17 +245,6 @@ struct ScoreArgs {
     BestArgs b;            // used by the last CTA when best != 0
 };
 
-struct TwoOptArgs {
-    int32_t n, m, ld, k;
-    const int32_t *nn;     // [n][k] neighbour lists (the candidate lists)
-    const int32_t *nnd;    // [n][k] distance to each neighbour
-    const int2 *xy;        // coordinates, or nullptr (then dist)
-    const int32_t *dist;   // [n][ld]
-    int32_t *tours;        // [m][ld], improved in place
-    int32_t *lens;         // [m]: read (iteration best) and written
-    uint32_t *err;         // device error bits
-};
-
 struct UpdateArgs {
     int32_t n, ld, cl, fullrow, evaporate;
     float persist;     // float(1 - rho)
@@ -294,8 +283,5 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
 cudaError_t launch_best(const BestArgs &a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s);
-size_t two_opt_smem(int n);
-cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, cudaStream_t s);
-cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s);
 
 }  // namespace mmas

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "twoopt.cuh"
 #include "mmas.h"
 
 using namespace mmas;

@@ -22,6 +22,7 @@
 #include <climits>
 
 #include "internal.cuh"
+#include "twoopt.cuh"
 
 namespace mmas {
 

@@ -1,0 +1,25 @@
+// Launch arguments and entry points of the 2-opt local search (Sec. 5.7),
+// kept apart from the construction / pheromone declarations.
+#pragma once
+
+#include "internal.cuh"
+
+namespace mmas {
+
+struct TwoOptArgs {
+    int32_t n, m, ld, k;
+    const int32_t *nn;     // [n][k] neighbour lists (the candidate lists)
+    const int32_t *nnd;    // [n][k] distance to each neighbour
+    const int2 *xy;        // coordinates, or nullptr (then dist)
+    const int32_t *dist;   // [n][ld]
+    int32_t *tours;        // [m][ld], improved in place
+    int32_t *lens;         // [m]: read (iteration best) and written
+    uint32_t *err;         // device error bits
+};
+
+// Dynamic shared memory one 2-opt CTA needs for an n-city tour.
+size_t two_opt_smem(int n);
+cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, cudaStream_t s);
+cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s);
+
+}  // namespace mmas
