@@ -202,10 +202,10 @@ mmas_status capture_iteration(mmas_handle *h)
         ScoreArgs sa = h->sargs;
         sa.best = 0;
         if (e == cudaSuccess) e = launch_score(sa, h->num_sms, cs);
-        if (e == cudaSuccess) e = launch_two_opt(h->targs, true, h->num_sms, cs);
+        if (e == cudaSuccess) e = launch_two_opt(h->targs, true, h->num_sms, h->smem_optin, cs);
         if (e == cudaSuccess) e = launch_best(h->bargs, cs);
     } else {
-        if (h->p.ls == 2 && e == cudaSuccess) e = launch_two_opt(h->targs, false, h->num_sms, cs);
+        if (h->p.ls == 2 && e == cudaSuccess) e = launch_two_opt(h->targs, false, h->num_sms, h->smem_optin, cs);
         if (e == cudaSuccess) e = launch_score(h->sargs, h->num_sms, cs);
     }
     if (e == cudaSuccess) e = launch_update(h->uargs, h->num_sms, cs);
@@ -335,9 +335,9 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
 
     TwoOptArgs &ta = h->targs;
     ta.n = n; ta.m = m; ta.ld = ld; ta.k = cl;
-    ta.nn = h->cand32; ta.xy = h->xy; ta.dist = h->dist; ta.tours = h->tours; ta.lens = h->lens;
+    ta.nn = h->cand32; ta.nn16 = h->cand16; ta.xy = h->xy; ta.dist = h->dist; ta.tours = h->tours; ta.lens = h->lens;
     ta.err = &h->sc->err;
-    if (h->p.ls > 0 && two_opt_smem(n) > h->smem_optin)
+    if (h->p.ls > 0 && two_opt_smem(n, cl, false) > (size_t)h->smem_optin)
         return fail(h, MMAS_EINVAL, "ls needs 13n bytes of shared memory per CTA: n is too large");
     if (h->p.ls > 0) {
         CK(h, dalloc(&h->nnd, (size_t)n * cl * sizeof(int32_t), h->stream));

@@ -4,21 +4,34 @@
 // One CTA improves one tour held in shared memory (tour and position of each
 // city, the length of each tour edge, don't-look bits: 13 bytes per city).
 // The sequential search visits the cities in index order, skipping those
-// whose don't-look bit is set; a city
-// without a move gets its bit set, a move clears the bits of its four cities
-// and the visit continues after the moving city; a run ends after a pass with
-// no move, and runs (from cleared bits) repeat until a run makes no move.
-// Here each round evaluates a window of consecutive cities in parallel against
-// the current tour and applies the lowest-index improving move; the window's
-// earlier cities had no move, so they get their bits set.  That is exactly the
-// sequential search, move for move, for any window size: the window is 32
-// cities after a move (moves come densely) and doubles, up to blockDim, while
-// windows find none.  A move reverses the shorter of the two paths it cuts,
-// with all threads.
+// whose don't-look bit is set; a city without a move gets its bit set, a move
+// clears the bits of its four cities and the visit continues after the moving
+// city; a run ends after a pass with no move, and runs (from cleared bits)
+// repeat until a run makes no move.
 //
-// Neighbour lists are the colony's candidate lists, with their distances
-// precomputed.  Distances are the exact integer ones (coordinates or the
-// explicit matrix).
+// Here each round evaluates a window of consecutive cities in parallel, one
+// warp per city (lane h examines neighbour h on both sides, and ballots pick
+// the first improving neighbour in list order), against the current tour, and
+// applies the lowest-index improving move; the window's earlier cities had no
+// move, so they get their bits set.  That is exactly the sequential search,
+// move for move, for any window size: the window is 32 cities after a move
+// (moves come densely) and doubles, up to blockDim, while windows find none.
+//
+// Round protocol.  A warp with a move publishes one 64-bit key (city, side,
+// the two positions) by atomic minimum, so the lowest city wins and every
+// thread can decode the whole move from the key.  Keys live in three rotating
+// slots: after the round's barrier a slot two rounds ahead is reset, which no
+// thread can still be reading, so a round without a move costs one barrier.
+// A move costs one more: a short one (the usual case) is applied by warp 0
+// alone -- bits of the skipped cities, the reversal, the two new edges, the
+// four cleared bits -- while the other warps wait; a long reversal uses every
+// thread and one extra barrier.
+//
+// Neighbour lists are the colony's candidate lists.  For the iteration-best
+// tour (one CTA) the coordinates and 16-bit lists are staged in shared memory
+// when they fit, so a neighbour costs shared loads only; otherwise neighbour
+// distances come from a table precomputed at set-up.  Distances are the exact
+// integer ones (coordinates or the explicit matrix).
 #include <climits>
 
 #include "internal.cuh"
@@ -28,81 +41,188 @@ namespace mmas {
 
 namespace {
 
-template <bool XY>
-__device__ __forceinline__ int32_t dij(const TwoOptArgs &a, int u, int v)
-{
-    if constexpr (XY)
-        return euc2d_exact(__ldg(a.xy + u), __ldg(a.xy + v));
-    else
-        return __ldg(a.dist + (size_t)u * a.ld + v);
-}
+constexpr unsigned long long NO_MOVE = ~0ull;
 
-// Shared-memory image of one tour: tour[i], pos[c], and
-// edge[i] = d(tour[i], tour[i+1 mod n]) kept exact under every move.
+// Shared-memory layout (byte offsets), identical on host and device.
+struct Layout {
+    uint32_t xy, nn, edge, tour, pos, dlb, total;
+    __host__ __device__ static Layout make(int n, int k, bool staged)
+    {
+        Layout L;
+        uint32_t off = 0;
+        L.xy = off;
+        if (staged) off += 8u * n;
+        off = (off + 15u) & ~15u;
+        L.nn = off;
+        if (staged) off += 2u * n * k;
+        off = (off + 15u) & ~15u;
+        L.edge = off;
+        off += 4u * n;
+        L.tour = off;
+        off += 4u * n;
+        L.pos = off;
+        off += 4u * n;
+        L.dlb = off;
+        off += n;
+        L.total = off + 16u;
+        return L;
+    }
+};
+
+// The tour image: tour[i], pos[c], edge[i] = d(tour[i], tour[i+1 mod n]).
 struct TourView {
-    int32_t *tour, *pos;
-    int32_t *edge;
+    int32_t *tour, *pos, *edge;
     int n;
     __device__ __forceinline__ int nxt(int i) const { return i + 1 == n ? 0 : i + 1; }
     __device__ __forceinline__ int prv(int i) const { return i == 0 ? n - 1 : i - 1; }
 };
 
-// First improving move at city c1: successor side, then predecessor side,
-// neighbours in list order while closer than the tour neighbour on that side.
-// mv = {u1, v1, u2, v2}: remove u1->v1 and u2->v2, add u1-u2 and v1-v2.
-// Tour-edge lengths come from the edge array, neighbour distances from the
-// precomputed lists; one distance is computed per neighbour examined.
-template <bool XY>
-__device__ __forceinline__ bool find_move(const TwoOptArgs &a, const TourView &tv, int c1,
-                                          int mv[4])
+// Distances and neighbour lists, from shared memory when staged.
+template <bool XY, bool STAGED>
+struct Geometry {
+    const TwoOptArgs &a;
+    const int2 *sxy;
+    const uint16_t *snn;
+    __device__ __forceinline__ int d(int u, int v) const
+    {
+        if constexpr (STAGED)
+            return euc2d_exact(sxy[u], sxy[v]);
+        else if constexpr (XY)
+            return euc2d_exact(__ldg(a.xy + u), __ldg(a.xy + v));
+        else
+            return __ldg(a.dist + (size_t)u * a.ld + v);
+    }
+    __device__ __forceinline__ int neighbour(int c, int h) const
+    {
+        if constexpr (STAGED)
+            return snn[c * a.k + h];
+        else
+            return __ldg(a.nn + (size_t)c * a.k + h);
+    }
+    // d(c, c2) for c2, neighbour h of c
+    __device__ __forceinline__ int neighbour_dist(int c, int h, int c2) const
+    {
+        if constexpr (STAGED)
+            return euc2d_exact(sxy[c], sxy[c2]);
+        else
+            return __ldg(a.nnd + (size_t)c * a.k + h);
+    }
+};
+
+// Key of a move at city c1: lower city first; side 0 = successor side (remove
+// c1->succ(c1) and c2->succ(c2)), side 1 = predecessor side (remove
+// pred(c1)->c1 and pred(c2)->c2); p = pos[c1], q = pos[c2] (15 bits each).
+__device__ __forceinline__ unsigned long long move_key(int c1, int side, int p, int q)
 {
-    const int p = tv.pos[c1];
-    const int s1 = tv.tour[tv.nxt(p)], p1 = tv.tour[tv.prv(p)];
-    const int32_t *nn = a.nn + (size_t)c1 * a.k;
-    const int32_t *dn = a.nnd + (size_t)c1 * a.k;
-    int radius = tv.edge[p];
-    for (int h = 0; h < a.k; ++h) {
-        const int d12 = __ldg(dn + h);
-        if (d12 >= radius) break;
-        const int c2 = __ldg(nn + h);
-        const int q = tv.pos[c2];
-        const int s2 = tv.tour[tv.nxt(q)];
-        const long long gain = (long long)radius + tv.edge[q] - d12 - dij<XY>(a, s1, s2);
-        if (gain > 0) {
-            mv[0] = c1; mv[1] = s1; mv[2] = c2; mv[3] = s2;
-            return true;
-        }
-    }
-    radius = tv.edge[tv.prv(p)];
-    for (int h = 0; h < a.k; ++h) {
-        const int d12 = __ldg(dn + h);
-        if (d12 >= radius) break;
-        const int c2 = __ldg(nn + h);
-        const int q = tv.pos[c2];
-        const int p2 = tv.tour[tv.prv(q)];
-        const long long gain = (long long)radius + tv.edge[tv.prv(q)] - d12 - dij<XY>(a, p1, p2);
-        if (gain > 0) {
-            mv[0] = p2; mv[1] = c2; mv[2] = p1; mv[3] = c1;
-            return true;
-        }
-    }
-    return false;
+    return ((unsigned long long)(uint32_t)c1 << 32) | ((uint32_t)side << 30) |
+           ((uint32_t)p << 15) | (uint32_t)q;
 }
 
-template <bool XY, bool IB>
+// First improving move at city c1, searched by one warp: lane h examines
+// neighbour h (h < k <= 32) on both sides.  The sequential scan of a side stops
+// at the first neighbour not closer than the tour neighbour on that side; the
+// lists are sorted by distance, so the neighbours it examines are exactly those
+// with d(c1, c2) below that radius, and its first improving one is the lowest
+// such lane whose gain is positive.  The successor side wins over the
+// predecessor side.  Every lane returns the same result.
+template <bool XY, bool STAGED>
+__device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geometry<XY, STAGED> &g,
+                                               const TourView &tv, int c1, int lane,
+                                               unsigned long long &key)
+{
+    const int p = tv.pos[c1];
+    const int pn = tv.nxt(p), pp = tv.prv(p);
+    const int s1 = tv.tour[pn], p1 = tv.tour[pp];
+    const int rs = tv.edge[p], rp = tv.edge[pp];
+    bool vs = false, vp = false;
+    int q = 0;
+    if (lane < a.k) {
+        const int c2 = g.neighbour(c1, lane);
+        const int d12 = g.neighbour_dist(c1, lane, c2);
+        q = tv.pos[c2];
+        const int qn = tv.nxt(q), qp = tv.prv(q);
+        const long long gs = (long long)rs + tv.edge[q] - d12 - g.d(s1, tv.tour[qn]);
+        const long long gp = (long long)rp + tv.edge[qp] - d12 - g.d(p1, tv.tour[qp]);
+        vs = d12 < rs && gs > 0;
+        vp = d12 < rp && gp > 0;
+    }
+    const unsigned ms = __ballot_sync(0xFFFFFFFFu, vs), mp = __ballot_sync(0xFFFFFFFFu, vp);
+    if ((ms | mp) == 0u) return false;
+    const int h = __ffs(ms ? ms : mp) - 1;
+    key = move_key(c1, ms ? 0 : 1, p, __shfl_sync(0xFFFFFFFFu, q, h));
+    return true;
+}
+
+// Moves whose reversed path has at most this many cities are applied by one warp.
+constexpr int SHORT_MOVE = 128;
+
+// Reverse tour[pa..pb] (len cities, cyclic) with `count` threads numbered
+// `t`; the len - 1 edges inside the path reverse with it.
+__device__ __forceinline__ void reverse_path(const TourView &tv, int pa, int pb, int len, int t,
+                                             int count)
+{
+    const int n = tv.n;
+    for (int s2 = t; s2 < len / 2; s2 += count) {
+        int i = pa + s2, j = pb - s2;
+        if (i >= n) i -= n;
+        if (j < 0) j += n;
+        const int ci = tv.tour[i], cj = tv.tour[j];
+        tv.tour[i] = cj;
+        tv.pos[cj] = i;
+        tv.tour[j] = ci;
+        tv.pos[ci] = j;
+    }
+    for (int s2 = t; s2 < (len - 1) / 2; s2 += count) {
+        int i = pa + s2, j = pb - 1 - s2;
+        if (i >= n) i -= n;
+        if (j < 0) j += n;
+        const int ei = tv.edge[i];
+        tv.edge[i] = tv.edge[j];
+        tv.edge[j] = ei;
+    }
+}
+
+// After the reversal of [pa..pb]: the two added edges border the path, and its
+// two ends with their outer neighbours are the move's four cities, whose
+// don't-look bits clear.
+template <bool XY, bool STAGED>
+__device__ __forceinline__ void finish_move(const Geometry<XY, STAGED> &g, const TourView &tv,
+                                            unsigned char *dlb, int pa, int pb)
+{
+    const int ia = tv.prv(pa), ib = tv.nxt(pb);
+    const int u = tv.tour[ia], v = tv.tour[pa], x = tv.tour[pb], y = tv.tour[ib];
+    tv.edge[ia] = g.d(u, v);
+    tv.edge[pb] = g.d(x, y);
+    dlb[u] = 0; dlb[v] = 0; dlb[x] = 0; dlb[y] = 0;
+}
+
+template <bool XY, bool STAGED, bool IB>
 __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
 {
-    extern __shared__ __align__(16) int32_t sm[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, tid = threadIdx.x, W = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, NW = W >> 5;
+    const Layout L = Layout::make(n, a.k, STAGED);
     TourView tv;
     tv.n = n;
-    tv.edge = sm;
-    tv.tour = sm + n;
-    tv.pos = sm + 2 * n;
-    unsigned char *s_dlb = reinterpret_cast<unsigned char *>(tv.pos + n);
-    __shared__ int s_first, s_red[32];
+    tv.edge = reinterpret_cast<int32_t *>(smem + L.edge);
+    tv.tour = reinterpret_cast<int32_t *>(smem + L.tour);
+    tv.pos = reinterpret_cast<int32_t *>(smem + L.pos);
+    unsigned char *s_dlb = smem + L.dlb;
+    const Geometry<XY, STAGED> g{a, reinterpret_cast<const int2 *>(smem + L.xy),
+                                 reinterpret_cast<const uint16_t *>(smem + L.nn)};
+    __shared__ unsigned long long s_key[3];
+    __shared__ int s_red[32];
     __shared__ unsigned long long s_best;
-    __shared__ int s_mv[4];
+
+    if constexpr (STAGED) {
+        int2 *sxy = reinterpret_cast<int2 *>(smem + L.xy);
+        for (int i = tid; i < n; i += W) sxy[i] = __ldg(a.xy + i);
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.nn16);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + L.nn);
+        const int chunks = (2 * n * a.k + 15) / 16;  // the list buffer is padded to 16 bytes
+        for (int i = tid; i < chunks; i += W) dst[i] = __ldg(src + i);
+    }
 
     int first_tour = blockIdx.x, tour_step = gridDim.x;
     if constexpr (IB) {
@@ -130,14 +250,16 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
             const int c = row[i];
             tv.tour[i] = c;
             tv.pos[c] = i;
-            tv.edge[i] = dij<XY>(a, c, row[i + 1 == n ? 0 : i + 1]);
+            tv.edge[i] = g.d(c, row[i + 1 == n ? 0 : i + 1]);
         }
+        if (tid < 3) s_key[tid] = NO_MOVE;
         __syncthreads();
         // every move shortens the tour by >= 1, so the search ends; the cap
         // (far above the moves a tour needs) only guards against a defect
         const long long cap = 64LL * n;
         long long total = 0;
         bool capped = false;
+        uint32_t round = 0;  // selects the key slot
         for (;;) {  // runs
             for (int i = tid; i < n; i += W) s_dlb[i] = 0;
             __syncthreads();
@@ -148,63 +270,64 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
                 int l = 0;
                 int w = 32;  // window: 32 cities after a move, doubling while none is found
                 while (l < n) {  // windows
-                    const int c1 = l + tid;
-                    const bool in = tid < w && c1 < n;
-                    int mv[4];
-                    const bool has = in && !s_dlb[c1] && find_move<XY>(a, tv, c1, mv);
-                    if (tid == 0) s_first = INT_MAX;
+                    const int wend = l + w < n ? l + w : n;
+                    unsigned long long mine = NO_MOVE;
+                    for (int c1 = l + warp; c1 < wend; c1 += NW) {  // warp-uniform
+                        if (s_dlb[c1]) continue;
+                        unsigned long long key;
+                        if (find_move_warp<XY, STAGED>(a, g, tv, c1, lane, key)) {
+                            mine = key;
+                            break;
+                        }
+                    }
+                    unsigned long long *slot = s_key + round % 3;
+                    if (lane == 0 && mine != NO_MOVE) atomicMin(slot, mine);
                     __syncthreads();
-                    if (has) atomicMin(&s_first, c1);
-                    __syncthreads();
-                    const int first = s_first;
-                    if (first == INT_MAX) {
-                        if (in) s_dlb[c1] = 1;
-                        l += w;
+                    const unsigned long long mk = *slot;
+                    if (tid == 0) s_key[(round + 2) % 3] = NO_MOVE;  // no one reads it for two rounds
+                    ++round;
+                    if (mk == NO_MOVE) {
+                        for (int c = l + tid; c < wend; c += W) s_dlb[c] = 1;
+                        l = wend;
                         w = w * 2 < W ? w * 2 : W;
-                        __syncthreads();
                         continue;
                     }
-                    w = 32;
-                    if (in && c1 < first) s_dlb[c1] = 1;  // evaluated, no move
-                    if (c1 == first) {
-                        s_mv[0] = mv[0]; s_mv[1] = mv[1]; s_mv[2] = mv[2]; s_mv[3] = mv[3];
+                    // cities [l, first) were evaluated without a move; every warp
+                    // stopped at its own first move, so all of them were reached
+                    const int first = (int)(mk >> 32);
+                    // decode: the path between the two removed edges, or its complement
+                    const int side = (int)((mk >> 30) & 1u);
+                    const int p = (int)((mk >> 15) & 0x7FFFu), q = (int)(mk & 0x7FFFu);
+                    int pa, pb, ca, cb;  // path [pa..pb]; complement [ca..cb]
+                    if (side == 0) {
+                        pa = tv.nxt(p); pb = q; ca = tv.nxt(q); cb = p;
+                    } else {
+                        pa = q; pb = tv.prv(p); ca = p; cb = tv.prv(q);
                     }
-                    __syncthreads();
-                    const int u1 = s_mv[0], v1 = s_mv[1], u2 = s_mv[2], v2 = s_mv[3];
-                    int pa = tv.pos[v1], pb = tv.pos[u2];
-                    int len = (pb - pa + n) % n + 1;
+                    int len = pb - pa + 1;
+                    if (len <= 0) len += n;
                     if (2 * len > n) {  // reverse the complementary, shorter path
-                        pa = tv.pos[v2];
-                        pb = tv.pos[u1];
+                        pa = ca;
+                        pb = cb;
                         len = n - len;
                     }
-                    __syncthreads();  // every thread has read the positions
-                    // reverse tour[pa..pb]; the len-1 edges inside it reverse too
-                    for (int s2 = tid; s2 < len / 2; s2 += W) {
-                        const int i = (pa + s2) % n, j = (pb - s2 + n) % n;
-                        const int ci = tv.tour[i], cj = tv.tour[j];
-                        tv.tour[i] = cj;
-                        tv.pos[cj] = i;
-                        tv.tour[j] = ci;
-                        tv.pos[ci] = j;
-                    }
-                    for (int s2 = tid; s2 < (len - 1) / 2; s2 += W) {
-                        const int i = (pa + s2) % n, j = (pb - 1 - s2 + n) % n;
-                        const int ei = tv.edge[i];
-                        tv.edge[i] = tv.edge[j];
-                        tv.edge[j] = ei;
-                    }
-                    __syncthreads();
-                    if (tid == 0) {
-                        s_dlb[u1] = 0; s_dlb[v1] = 0; s_dlb[u2] = 0; s_dlb[v2] = 0;
-                        // the two added edges now border the reversed path
-                        const int ia = tv.prv(pa);
-                        tv.edge[ia] = dij<XY>(a, tv.tour[ia], tv.tour[pa]);
-                        tv.edge[pb] = dij<XY>(a, tv.tour[pb], tv.tour[tv.nxt(pb)]);
+                    if (len <= SHORT_MOVE) {
+                        if (warp == 0) {
+                            for (int c = l + lane; c < first; c += 32) s_dlb[c] = 1;
+                            reverse_path(tv, pa, pb, len, lane, 32);
+                            __syncwarp();
+                            if (lane == 0) finish_move(g, tv, s_dlb, pa, pb);
+                        }
+                    } else {
+                        for (int c = l + tid; c < first; c += W) s_dlb[c] = 1;
+                        reverse_path(tv, pa, pb, len, tid, W);
+                        __syncthreads();
+                        if (tid == 0) finish_move(g, tv, s_dlb, pa, pb);
                     }
                     improved = true;
                     ++run_moves;
                     l = first + 1;
+                    w = 32;
                     __syncthreads();
                     if (++total > cap) {
                         if (tid == 0) atomicOr(a.err, ERR_LS_CAP);
@@ -237,17 +360,28 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
 template <bool XY>
 __global__ void k_neighbour_dist(const TwoOptArgs a, int32_t *nnd)
 {
+    const Geometry<XY, false> g{a, nullptr, nullptr};
     const size_t total = (size_t)a.n * a.k;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / a.k);
-        nnd[e] = dij<XY>(a, c, a.nn[e]);
+        nnd[e] = g.d(c, a.nn[e]);
     }
+}
+
+template <bool XY, bool STAGED, bool IB>
+cudaError_t launch_one(const TwoOptArgs &a, int grid, int threads, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_two_opt<XY, STAGED, IB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_two_opt<XY, STAGED, IB><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t two_opt_smem(int n) { return (size_t)13 * n + 16; }
+size_t two_opt_smem(int n, int k, bool staged) { return Layout::make(n, k, staged).total; }
 
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s)
 {
@@ -258,30 +392,22 @@ cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, cudaStream_t s)
+cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, int smem_optin,
+                           cudaStream_t s)
 {
-    const size_t smem = two_opt_smem(a.n);
-    const void *fn;
-    int threads, grid;
     if (iteration_best) {
-        fn = a.xy ? (const void *)k_two_opt<true, true> : (const void *)k_two_opt<false, true>;
-        threads = 1024;
-        grid = 1;
-    } else {
-        fn = a.xy ? (const void *)k_two_opt<true, false> : (const void *)k_two_opt<false, false>;
-        threads = 256;
-        grid = a.m < num_sms * 8 ? a.m : num_sms * 8;
+        // one tour, one CTA: stage coordinates and lists when they fit
+        const bool staged = a.xy && two_opt_smem(a.n, a.k, true) <= (size_t)smem_optin;
+        const size_t smem = two_opt_smem(a.n, a.k, staged);
+        if (staged) return launch_one<true, true, true>(a, 1, 1024, smem, s);
+        if (a.xy) return launch_one<true, false, true>(a, 1, 1024, smem, s);
+        return launch_one<false, false, true>(a, 1, 1024, smem, s);
     }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (iteration_best) {
-        if (a.xy) k_two_opt<true, true><<<grid, threads, smem, s>>>(a);
-        else k_two_opt<false, true><<<grid, threads, smem, s>>>(a);
-    } else {
-        if (a.xy) k_two_opt<true, false><<<grid, threads, smem, s>>>(a);
-        else k_two_opt<false, false><<<grid, threads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    // every tour: one CTA of 256 threads per tour, many per SM
+    const size_t smem = two_opt_smem(a.n, a.k, false);
+    const int grid = a.m < num_sms * 8 ? a.m : num_sms * 8;
+    if (a.xy) return launch_one<true, false, false>(a, grid, 256, smem, s);
+    return launch_one<false, false, false>(a, grid, 256, smem, s);
 }
 
 }  // namespace mmas

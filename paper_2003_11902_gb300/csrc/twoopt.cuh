@@ -9,6 +9,7 @@ namespace mmas {
 struct TwoOptArgs {
     int32_t n, m, ld, k;
     const int32_t *nn;     // [n][k] neighbour lists (the candidate lists)
+    const uint16_t *nn16;  // the same lists as 16-bit ids (padded to 16 bytes)
     const int32_t *nnd;    // [n][k] distance to each neighbour
     const int2 *xy;        // coordinates, or nullptr (then dist)
     const int32_t *dist;   // [n][ld]
@@ -17,9 +18,11 @@ struct TwoOptArgs {
     uint32_t *err;         // device error bits
 };
 
-// Dynamic shared memory one 2-opt CTA needs for an n-city tour.
-size_t two_opt_smem(int n);
-cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, cudaStream_t s);
+// Dynamic shared memory of one 2-opt CTA for an n-city tour with k
+// neighbours; `staged` adds the coordinates and the 16-bit neighbour lists.
+size_t two_opt_smem(int n, int k, bool staged);
+cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, int smem_optin,
+                           cudaStream_t s);
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s);
 
 }  // namespace mmas

@@ -62,6 +62,22 @@ def test_setup_matches_oracle(n, cl, src):
     g.close()
 
 
+def test_distances_exact_across_scales():
+    """Rounded Euclidean distances over every scale of the fast estimate's range
+    (s < 2^36) and beyond it (the double-precision path, d >= 2^18): all pairs
+    of points spread from unit spacing to ~3M apart (n * max d < 2^31) equal the
+    oracle's integer ones."""
+    rng = np.random.default_rng(123)
+    pts = [rng.integers(0, 1 << 17, size=(300, 2)),        # s < 2^35
+           rng.integers(0, 64, size=(100, 2)),             # small, many ties
+           rng.integers(0, 1 << 21, size=(100, 2)),        # many pairs with s >= 2^36
+           np.array([[0, 0], [1, 1], [3, 4], [4, 2], [181, 181], [(1 << 18) - 1, 0], [1 << 18, 0]])]
+    xy = np.unique(np.concatenate(pts).astype(np.int32), axis=0)
+    g, o = _pair(xy=xy, m=2, cl=4, seed=1)
+    assert np.array_equal(g.setup()["d"], o.state()["d"])
+    g.close()
+
+
 def test_setup_clustered_3800():
     xy = I.clustered(3800, 3)
     g, o = _pair(xy=xy, m=4, cl=16, seed=1)
@@ -344,12 +360,18 @@ def test_phase_timing_is_a_pure_measurement():
 @pytest.mark.parametrize("kind,n,m,cl,ls,iters", [
     ("uniform", 50, 20, 8, 2, 3),        # every ant, 256-city windows
     ("uniform", 1000, 48, 32, 2, 1),     # every ant at the n = 1000 size
-    ("uniform", 300, 40, 16, 1, 5),      # the iteration best, 1024-city windows
-    ("clustered", 3800, 64, 16, 1, 1),   # the clustered n = 3800 shape, iteration best
+    ("uniform", 300, 40, 16, 1, 5),      # the iteration best, staged lists, 1024-city windows
+    ("clustered", 3800, 64, 16, 1, 1),   # the clustered n = 3800 shape, iteration best (staged)
+    ("uniform", 3000, 24, 32, 1, 1),     # iteration best too large to stage
+    ("dist", 400, 24, 16, 1, 2),         # explicit matrix, iteration best
+    ("dist", 400, 24, 16, 2, 1),         # explicit matrix, every ant
 ])
 def test_two_opt_matches_oracle(kind, n, m, cl, ls, iters):
-    xy = I.uniform(n, 400 + n) if kind == "uniform" else I.clustered(n, 3)
-    g, o = _pair(xy=xy, m=m, cl=cl, rho=0.1, seed=6, ls=ls)
+    xy = I.clustered(n, 3) if kind == "clustered" else I.uniform(n, 400 + n)
+    if kind == "dist":
+        g, o = _pair(dist=O.distances(xy), m=m, cl=cl, rho=0.1, seed=6, ls=ls)
+    else:
+        g, o = _pair(xy=xy, m=m, cl=cl, rho=0.1, seed=6, ls=ls)
     for it in range(iters):
         g.iterate(1)
         o.iterate(1)
