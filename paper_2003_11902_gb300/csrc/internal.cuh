@@ -99,34 +99,6 @@ __device__ __forceinline__ uint32_t ord_key(float f)
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-// TSPLIB rounded Euclidean distance r = nint(sqrt(s)), s = dx^2 + dy^2, exact.
-// r is the integer with r^2 - r < s <= r^2 + r (sqrt(s) is never a
-// half-integer).  Below s = 2^36 the single-precision estimate s * rsqrt(s)
-// (relative error under 2^-21) is within 0.1 of sqrt(s), so it rounds to r or
-// r +- 1, and one integer comparison on each side settles r.  Above that
-// (points ~2^18 apart or more) q = floor(sqrt(s)) comes from the double square
-// root with integer correction, and r = q + [s > q^2 + q].  |coords| < 2^30
-// keeps s below 2^63.
-__device__ __forceinline__ int32_t euc2d_exact(int2 a, int2 b)
-{
-    const long long dx = (long long)a.x - b.x, dy = (long long)a.y - b.y;
-    const unsigned long long s = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
-    if (s < (1ull << 36)) {
-        const float fx = (float)dx, fy = (float)dy;  // |dx|, |dy| < 2^18: exact
-        const float fs = __fmaf_rn(fx, fx, __fmul_rn(fy, fy));
-        const float est = fs > 0.0f ? __fmul_rn(fs, rsqrtf(fs)) : 0.0f;
-        const uint32_t r0 = (uint32_t)__float2int_rn(est);
-        const unsigned long long r2 = (unsigned long long)r0 * r0;
-        const uint32_t up = s > r2 + r0 ? 1u : 0u;
-        const uint32_t down = (r0 > 0u && s <= r2 - r0) ? 1u : 0u;
-        return (int32_t)(r0 + up - down);
-    }
-    unsigned long long q = (unsigned long long)sqrt((double)s);
-    while (q * q > s) --q;
-    while ((q + 1) * (q + 1) <= s) ++q;
-    return (int32_t)(q + (s > q * q + q ? 1ull : 0ull));
-}
-
 // Trail limits (after Stuetzle and Hoos, as Sec. 5 states): tau_max = 1/(rho C),
 // tau_min = tau_max (1 - p)/((n/2 - 1) p), capped at tau_max; double, stored float.
 __device__ __forceinline__ void trail_limits(int32_t n, double rho, double p_root, long long cost, float *tmax,

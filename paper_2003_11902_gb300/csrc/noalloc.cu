@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 
+#include "distance.cuh"
 #include "internal.cuh"
 #include "mmas.h"
 

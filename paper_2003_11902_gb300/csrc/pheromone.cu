@@ -15,6 +15,7 @@
 // they are one pass, so each cell is read and written once per iteration.
 #include <climits>
 
+#include "distance.cuh"
 #include "internal.cuh"
 
 namespace mmas {

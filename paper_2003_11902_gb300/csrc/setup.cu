@@ -3,6 +3,7 @@
 // the initial trail limits and tau <- tau_max.  Run once per mmas_create.
 #include <climits>
 
+#include "distance.cuh"
 #include "internal.cuh"
 
 namespace mmas {

@@ -14,18 +14,21 @@
 // the first improving neighbour in list order), against the current tour, and
 // applies the lowest-index improving move; the window's earlier cities had no
 // move, so they get their bits set.  That is exactly the sequential search,
-// move for move, for any window size: the window is 32 cities after a move
-// (moves come densely) and doubles, up to blockDim, while windows find none.
+// move for move, for any window size: the window is FIRST_WINDOW cities after
+// a move (moves come densely, so a small window wastes few evaluations and
+// leaves the other warps idle) and doubles, up to blockDim, while windows find
+// none.
 //
-// Round protocol.  A warp with a move publishes one 64-bit key (city, side,
-// the two positions) by atomic minimum, so the lowest city wins and every
-// thread can decode the whole move from the key.  Keys live in three rotating
-// slots: after the round's barrier a slot two rounds ahead is reset, which no
-// thread can still be reading, so a round without a move costs one barrier.
-// A move costs one more: a short one (the usual case) is applied by warp 0
-// alone -- bits of the skipped cities, the reversal, the two new edges, the
-// four cleared bits -- while the other warps wait; a long reversal uses every
-// thread and one extra barrier.
+// Round protocol.  A warp with a move records it in its own slot (city, side,
+// the two positions, the two new edge lengths) and publishes its city by
+// atomic minimum, so the lowest city wins; the winner's slot then describes
+// the whole move.  The minima live in three rotating words: after the round's
+// barrier a word two rounds ahead is reset, which no thread can still be
+// reading, so a round without a move costs one barrier.
+// A move costs one more: warp 0 alone applies it -- bits of the skipped
+// cities, the reversal of the shorter path (18 cities on average on the
+// clustered n = 3800 workload), the two new edges, the four cleared bits --
+// while the other warps wait at the barrier.
 //
 // Neighbour lists are the colony's candidate lists.  For the iteration-best
 // tour (one CTA) the coordinates and 16-bit lists are staged in shared memory
@@ -34,6 +37,7 @@
 // integer ones (coordinates or the explicit matrix).
 #include <climits>
 
+#include "distance.cuh"
 #include "internal.cuh"
 #include "twoopt.cuh"
 
@@ -41,7 +45,6 @@ namespace mmas {
 
 namespace {
 
-constexpr unsigned long long NO_MOVE = ~0ull;
 
 // Shared-memory layout (byte offsets), identical on host and device.
 struct Layout {
@@ -109,14 +112,13 @@ struct Geometry {
     }
 };
 
-// Key of a move at city c1: lower city first; side 0 = successor side (remove
-// c1->succ(c1) and c2->succ(c2)), side 1 = predecessor side (remove
-// pred(c1)->c1 and pred(c2)->c2); p = pos[c1], q = pos[c2] (15 bits each).
-__device__ __forceinline__ unsigned long long move_key(int c1, int side, int p, int q)
-{
-    return ((unsigned long long)(uint32_t)c1 << 32) | ((uint32_t)side << 30) |
-           ((uint32_t)p << 15) | (uint32_t)q;
-}
+// A move at city c1.  side 0 = successor side (remove c1->succ(c1) and
+// c2->succ(c2), add c1-c2 and succ(c1)-succ(c2)); side 1 = predecessor side
+// (remove pred(c1)->c1 and pred(c2)->c2, add c1-c2 and pred(c1)-pred(c2));
+// p = pos[c1], q = pos[c2]; d12 = d(c1, c2) and d34 the other added edge.
+struct Move {
+    int32_t c1, side, p, q, d12, d34;
+};
 
 // First improving move at city c1, searched by one warp: lane h examines
 // neighbour h (h < k <= 32) on both sides.  The sequential scan of a side stops
@@ -127,34 +129,38 @@ __device__ __forceinline__ unsigned long long move_key(int c1, int side, int p, 
 // predecessor side.  Every lane returns the same result.
 template <bool XY, bool STAGED>
 __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geometry<XY, STAGED> &g,
-                                               const TourView &tv, int c1, int lane,
-                                               unsigned long long &key)
+                                               const TourView &tv, int c1, int lane, Move &mv)
 {
     const int p = tv.pos[c1];
     const int pn = tv.nxt(p), pp = tv.prv(p);
     const int s1 = tv.tour[pn], p1 = tv.tour[pp];
     const int rs = tv.edge[p], rp = tv.edge[pp];
     bool vs = false, vp = false;
-    int q = 0;
+    int q = 0, d12 = 0, dss = 0, dpp = 0;
     if (lane < a.k) {
         const int c2 = g.neighbour(c1, lane);
-        const int d12 = g.neighbour_dist(c1, lane, c2);
+        d12 = g.neighbour_dist(c1, lane, c2);
         q = tv.pos[c2];
         const int qn = tv.nxt(q), qp = tv.prv(q);
-        const long long gs = (long long)rs + tv.edge[q] - d12 - g.d(s1, tv.tour[qn]);
-        const long long gp = (long long)rp + tv.edge[qp] - d12 - g.d(p1, tv.tour[qp]);
-        vs = d12 < rs && gs > 0;
-        vp = d12 < rp && gp > 0;
+        dss = g.d(s1, tv.tour[qn]);
+        dpp = g.d(p1, tv.tour[qp]);
+        vs = d12 < rs && (long long)rs + tv.edge[q] - d12 - dss > 0;
+        vp = d12 < rp && (long long)rp + tv.edge[qp] - d12 - dpp > 0;
     }
     const unsigned ms = __ballot_sync(0xFFFFFFFFu, vs), mp = __ballot_sync(0xFFFFFFFFu, vp);
     if ((ms | mp) == 0u) return false;
     const int h = __ffs(ms ? ms : mp) - 1;
-    key = move_key(c1, ms ? 0 : 1, p, __shfl_sync(0xFFFFFFFFu, q, h));
+    mv.c1 = c1;
+    mv.side = ms ? 0 : 1;
+    mv.p = p;
+    mv.q = __shfl_sync(0xFFFFFFFFu, q, h);
+    mv.d12 = __shfl_sync(0xFFFFFFFFu, d12, h);
+    mv.d34 = __shfl_sync(0xFFFFFFFFu, ms ? dss : dpp, h);
     return true;
 }
 
-// Moves whose reversed path has at most this many cities are applied by one warp.
-constexpr int SHORT_MOVE = 128;
+// Cities in the first window after a move.
+constexpr int FIRST_WINDOW = 8;
 
 // Reverse tour[pa..pb] (len cities, cyclic) with `count` threads numbered
 // `t`; the len - 1 edges inside the path reverse with it.
@@ -184,20 +190,48 @@ __device__ __forceinline__ void reverse_path(const TourView &tv, int pa, int pb,
 
 // After the reversal of [pa..pb]: the two added edges border the path, and its
 // two ends with their outer neighbours are the move's four cities, whose
-// don't-look bits clear.
-template <bool XY, bool STAGED>
-__device__ __forceinline__ void finish_move(const Geometry<XY, STAGED> &g, const TourView &tv,
-                                            unsigned char *dlb, int pa, int pb)
+// don't-look bits clear.  Whichever of the two paths was reversed, the edge
+// before it is c1-c2 (successor side) or pred(c1)-pred(c2) (predecessor
+// side), and the edge after it the other one.
+__device__ __forceinline__ void finish_move(const TourView &tv, unsigned char *dlb, const Move &mv,
+                                            int pa, int pb)
 {
     const int ia = tv.prv(pa), ib = tv.nxt(pb);
+    tv.edge[ia] = mv.side ? mv.d34 : mv.d12;
+    tv.edge[pb] = mv.side ? mv.d12 : mv.d34;
     const int u = tv.tour[ia], v = tv.tour[pa], x = tv.tour[pb], y = tv.tour[ib];
-    tv.edge[ia] = g.d(u, v);
-    tv.edge[pb] = g.d(x, y);
     dlb[u] = 0; dlb[v] = 0; dlb[x] = 0; dlb[y] = 0;
 }
 
+// One warp applies move mv: the window's cities before mv.c1 get
+// their bits set, then the shorter of the two paths between the removed edges
+// is reversed and the move's edges and bits are updated.
+__device__ __forceinline__ void apply_move(const TourView &tv, unsigned char *dlb, const Move &mv,
+                                           int l, int lane)
+{
+    const int n = tv.n;
+    for (int c = l + lane; c < mv.c1; c += 32) dlb[c] = 1;
+    const int p = mv.p, q = mv.q;
+    int pa, pb, ca, cb;  // path [pa..pb]; complement [ca..cb]
+    if (mv.side == 0) {
+        pa = tv.nxt(p); pb = q; ca = tv.nxt(q); cb = p;
+    } else {
+        pa = q; pb = tv.prv(p); ca = p; cb = tv.prv(q);
+    }
+    int len = pb - pa + 1;
+    if (len <= 0) len += n;
+    if (2 * len > n) {
+        pa = ca;
+        pb = cb;
+        len = n - len;
+    }
+    reverse_path(tv, pa, pb, len, lane, 32);
+    __syncwarp();
+    if (lane == 0) finish_move(tv, dlb, mv, pa, pb);
+}
+
 template <bool XY, bool STAGED, bool IB>
-__global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
+__global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, tid = threadIdx.x, W = blockDim.x;
@@ -211,7 +245,8 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
     unsigned char *s_dlb = smem + L.dlb;
     const Geometry<XY, STAGED> g{a, reinterpret_cast<const int2 *>(smem + L.xy),
                                  reinterpret_cast<const uint16_t *>(smem + L.nn)};
-    __shared__ unsigned long long s_key[3];
+    __shared__ int s_first[3];
+    __shared__ Move s_move[32];  // per warp
     __shared__ int s_red[32];
     __shared__ unsigned long long s_best;
 
@@ -252,7 +287,7 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
             tv.pos[c] = i;
             tv.edge[i] = g.d(c, row[i + 1 == n ? 0 : i + 1]);
         }
-        if (tid < 3) s_key[tid] = NO_MOVE;
+        if (tid < 3) s_first[tid] = INT_MAX;
         __syncthreads();
         // every move shortens the tour by >= 1, so the search ends; the cap
         // (far above the moves a tour needs) only guards against a defect
@@ -268,66 +303,39 @@ __global__ void __launch_bounds__(1024) k_two_opt(const TwoOptArgs a)
             while (improved && !capped) {  // passes
                 improved = false;
                 int l = 0;
-                int w = 32;  // window: 32 cities after a move, doubling while none is found
+                int w = FIRST_WINDOW;  // cities in the window; doubles while none has a move
                 while (l < n) {  // windows
                     const int wend = l + w < n ? l + w : n;
-                    unsigned long long mine = NO_MOVE;
+                    int mine = INT_MAX;
                     for (int c1 = l + warp; c1 < wend; c1 += NW) {  // warp-uniform
                         if (s_dlb[c1]) continue;
-                        unsigned long long key;
-                        if (find_move_warp<XY, STAGED>(a, g, tv, c1, lane, key)) {
-                            mine = key;
+                        Move mv;
+                        if (find_move_warp<XY, STAGED>(a, g, tv, c1, lane, mv)) {
+                            if (lane == 0) s_move[warp] = mv;
+                            mine = c1;
                             break;
                         }
                     }
-                    unsigned long long *slot = s_key + round % 3;
-                    if (lane == 0 && mine != NO_MOVE) atomicMin(slot, mine);
+                    int *slot = s_first + round % 3;
+                    if (lane == 0 && mine != INT_MAX) atomicMin(slot, mine);
                     __syncthreads();
-                    const unsigned long long mk = *slot;
-                    if (tid == 0) s_key[(round + 2) % 3] = NO_MOVE;  // no one reads it for two rounds
+                    const int first = *slot;
+                    if (tid == 0) s_first[(round + 2) % 3] = INT_MAX;  // no one reads it for two rounds
                     ++round;
-                    if (mk == NO_MOVE) {
+                    if (first == INT_MAX) {
                         for (int c = l + tid; c < wend; c += W) s_dlb[c] = 1;
                         l = wend;
                         w = w * 2 < W ? w * 2 : W;
                         continue;
                     }
-                    // cities [l, first) were evaluated without a move; every warp
-                    // stopped at its own first move, so all of them were reached
-                    const int first = (int)(mk >> 32);
-                    // decode: the path between the two removed edges, or its complement
-                    const int side = (int)((mk >> 30) & 1u);
-                    const int p = (int)((mk >> 15) & 0x7FFFu), q = (int)(mk & 0x7FFFu);
-                    int pa, pb, ca, cb;  // path [pa..pb]; complement [ca..cb]
-                    if (side == 0) {
-                        pa = tv.nxt(p); pb = q; ca = tv.nxt(q); cb = p;
-                    } else {
-                        pa = q; pb = tv.prv(p); ca = p; cb = tv.prv(q);
-                    }
-                    int len = pb - pa + 1;
-                    if (len <= 0) len += n;
-                    if (2 * len > n) {  // reverse the complementary, shorter path
-                        pa = ca;
-                        pb = cb;
-                        len = n - len;
-                    }
-                    if (len <= SHORT_MOVE) {
-                        if (warp == 0) {
-                            for (int c = l + lane; c < first; c += 32) s_dlb[c] = 1;
-                            reverse_path(tv, pa, pb, len, lane, 32);
-                            __syncwarp();
-                            if (lane == 0) finish_move(g, tv, s_dlb, pa, pb);
-                        }
-                    } else {
-                        for (int c = l + tid; c < first; c += W) s_dlb[c] = 1;
-                        reverse_path(tv, pa, pb, len, tid, W);
-                        __syncthreads();
-                        if (tid == 0) finish_move(g, tv, s_dlb, pa, pb);
-                    }
+                    // cities [l, first) were evaluated without a move (every warp
+                    // stopped at its own first move, so all of them were reached);
+                    // city c was searched by warp (c - l) mod NW
+                    if (warp == 0) apply_move(tv, s_dlb, s_move[(first - l) & (NW - 1)], l, lane);
                     improved = true;
                     ++run_moves;
                     l = first + 1;
-                    w = 32;
+                    w = FIRST_WINDOW;
                     __syncthreads();
                     if (++total > cap) {
                         if (tid == 0) atomicOr(a.err, ERR_LS_CAP);
