@@ -233,6 +233,80 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
     for (int j = 0; j < 4; ++j) lg[j] = nl[j];
 }
 
+// A full group of four steps (t = 4g .. 4g+3, all inside the tour) without a
+// branch: a step whose candidates are all visited freezes the rest of the
+// group (no mark, no tour entry, cur unchanged), so the four steps and the
+// next group's generator work form one straight-line block the compiler can
+// interleave.  Only a frozen group leaves the block: that step takes the
+// out-of-line fallback and the group's remaining steps run one by one.  The
+// result equals cand_group's step for step.
+template <bool REGMASK>
+__device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const uint16_t *cc,
+                                                const float *cw, Tabu<REGMASK> &tb, int lane,
+                                                int ant, uint32_t it, int g, float (&lg)[4],
+                                                int &cur, int &twin, uint32_t &fbn)
+{
+    uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
+    float nl[4];
+    const int tb32 = (4 * g) & 31;
+    const bool act = lane < a.cl;
+    bool live = true;  // warp-uniform
+    int jfail = 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (j == 0) philox_rounds_rk<0, 4>(nx, a.rk0, a.rk1);
+        if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
+        if (j == 2) {
+            philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
+            nl[0] = log2f(unit_open(nx.x));
+            nl[1] = log2f(unit_open(nx.y));
+        }
+        if (j == 3) {
+            nl[2] = log2f(unit_open(nx.z));
+            nl[3] = log2f(unit_open(nx.w));
+        }
+        const int idx = act ? cur * a.cl + lane : 0;
+        const uint32_t v = cc[idx];
+        const float wi = cw[idx];
+        const uint32_t word = tb.word_of((int)v);
+        const bool ok = act && !((word >> (v & 31)) & 1u);
+        const uint32_t k = ok ? ord_key(__fmul_rn(lg[j], wi)) : 0u;
+        const uint32_t mx = __reduce_max_sync(FULL, k);
+        const uint32_t nxt = __reduce_min_sync(FULL, (k == mx && mx != 0u) ? v : 0xFFFFFFFFu);
+        jfail = (live && mx == 0u) ? j : jfail;
+        live = live && mx != 0u;
+        if constexpr (REGMASK) {
+            tb.reg |= (live && (int)(nxt >> 5) == lane) ? (1u << (nxt & 31)) : 0u;
+        } else {
+            if (live) tb.mark(lane, (int)nxt);
+        }
+        twin = (live && lane == tb32 + j) ? (int)nxt : twin;
+        cur = live ? (int)nxt : cur;
+    }
+    if (__builtin_expect(jfail < 4, 0)) {
+        // step 4g + jfail: every candidate of cur is visited
+        ++fbn;
+        const int t = 4 * g + jfail;
+        const int fb = cand_fallback<REGMASK>(a.wmat + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane,
+                                              a.fallback, (uint32_t)t, (uint32_t)ant, it, a.key0,
+                                              a.key1, &a.sc->err, cur);
+        tb.mark(lane, fb);
+        twin = (lane == tb32 + jfail) ? fb : twin;
+        cur = fb;
+#pragma unroll
+        for (int j = 1; j < 4; ++j) {
+            if (j <= jfail) continue;
+            const int next = cand_step<REGMASK>(a, cc, cw, tb, lane, cur, lg[j], 4 * g + j, ant,
+                                                it, fbn);
+            tb.mark(lane, next);
+            twin = (lane == tb32 + j) ? next : twin;
+            cur = next;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
+}
+
 template <int MODE, bool STAGED, bool REGMASK>
 __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
@@ -306,8 +380,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
             cand_group<true, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
             int g = 1;
             for (; 4 * g + 3 <= a.n - 1; ++g) {
-                cand_group<false, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin,
-                                           fbn);
+                cand_group_spec<REGMASK>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
                 if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
             }
             if (4 * g <= a.n - 1)
