@@ -211,6 +211,79 @@ mmas_status mmas_enable_phase_timing(mmas_handle *h, int32_t enable);
  * timed iteration has run. */
 mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms, float *total_ms);
 
+/* ---- batched colonies -----------------------------------------------------
+ *
+ * Many independent colonies, on instances of uneven size, advanced together.
+ * Every iteration (Alg. 1) of all of them is three launches, recorded once as
+ * a CUDA graph: one persistent construction launch that hands (colony, group of
+ * ants) chunks to CTAs from a global counter, largest colonies first, staging
+ * each colony's candidate table in shared memory when it fits; one scoring
+ * launch (lengths, then each colony's iteration best, global best and limits);
+ * one fused pheromone launch over the rows of every colony.
+ *
+ * Colony b is exactly the colony mmas_create would build from instances[b]
+ * with the shared params, except seed = params.seed + b and m = params.m (n_b
+ * when params.m is 0): same tours, lengths and pheromone, iteration by
+ * iteration, whatever the launch configuration.  Restrictions: 1 <= cl <= 32
+ * (candidate lists), ls = 0, ant_offset = 0; either every instance has
+ * coordinates or every instance has a matrix.  count >= 1.  The batch
+ * enqueues on params.stream (NULL: a private non-blocking stream).
+ * Errors: EINVAL (a restriction or an instance's validation fails; the message
+ * names the colony), ENOMEM, ECUDA; on error nothing is created. */
+typedef struct mmas_batch mmas_batch;
+
+/* Launch shape of the batched construction: warps (= ants) per CTA, 1..12,
+ * and CTAs per SM, 1..4 (shared memory per CTA is the SM's share).  Results do
+ * not depend on it. */
+typedef struct {
+    int32_t warps_per_cta;
+    int32_t ctas_per_sm;
+} mmas_batch_config;
+
+mmas_status mmas_batch_create(const mmas_instance *instances, int32_t count,
+                              const mmas_params *params, mmas_batch **out);
+
+/* Enqueue k iterations of every colony (k >= 0). */
+mmas_status mmas_batch_iterate(mmas_batch *b, int32_t k);
+
+/* Synchronise; copy colony c's global best tour (n_c ids) and length.  ESTATE
+ * before the first iteration.  Either pointer may be NULL. */
+mmas_status mmas_batch_best_tour(mmas_batch *b, int32_t colony, int32_t *tour_out,
+                                 int32_t *len_out);
+
+/* Synchronise; copy every colony's global best length (count int32, -1 before
+ * the first iteration) in one transfer. */
+mmas_status mmas_batch_best_lengths(mmas_batch *b, int32_t *lens_out);
+
+/* Synchronise; copy colony c's last tours (m_c x n_c) and lengths (m_c).
+ * Either pointer may be NULL. */
+mmas_status mmas_batch_get_tours(mmas_batch *b, int32_t colony, int32_t *tours, int32_t *lens);
+
+/* Use launch shape *cfg for the construction (re-records the graph). */
+mmas_status mmas_batch_set_config(mmas_batch *b, const mmas_batch_config *cfg);
+mmas_status mmas_batch_get_config(mmas_batch *b, mmas_batch_config *cfg);
+
+/* Autotuner: time the construction launch under each candidate launch shape
+ * (reps launches each, median; the colonies' pheromone and iteration indices
+ * are untouched and the tours are rebuilt by the next iteration), keep the
+ * fastest and write it to *chosen (may be NULL).  Fallback counters are reset. */
+mmas_status mmas_batch_autotune(mmas_batch *b, int32_t reps, mmas_batch_config *chosen);
+
+/* Block until the batch's work is done; report device-side errors. */
+mmas_status mmas_batch_synchronize(mmas_batch *b);
+
+/* Phase timing as for one colony: construction vs. the rest, for the most
+ * recent iteration run by mmas_batch_iterate with timing on. */
+mmas_status mmas_batch_enable_phase_timing(mmas_batch *b, int32_t enable);
+mmas_status mmas_batch_phase_times(mmas_batch *b, float *construct_ms, float *rest_ms,
+                                   float *total_ms);
+
+/* Sum of the colonies' fallback steps since creation (or the last autotune). */
+mmas_status mmas_batch_fallback_steps(mmas_batch *b, int64_t *out);
+
+void mmas_batch_destroy(mmas_batch *b);
+const char *mmas_batch_last_error(const mmas_batch *b);
+
 /* ---- allocation-free scoring ----------------------------------------------
  *
  * For callers that must not have a library allocate device memory: serving

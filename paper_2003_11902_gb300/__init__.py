@@ -3,16 +3,17 @@
 Solution construction (candidate lists, bitmask tabu, weighted reservoir
 sampling), tour lengths, iteration/global best with trail limits, and the fused
 evaporation/deposit/choice_info pass, as hand-written CUDA for sm_103a behind
-the C ABI in include/mmas.h.  ``mmas`` is the Python binding; ``instances``
+the C ABI in include/mmas.h; 2-opt local search; batches of colonies advanced
+by shared launches.  ``mmas`` is the Python binding; ``instances``
 draws seeded synthetic inputs.
 """
 from . import instances
-from .mmas import (Colony, MMASError, load, mmas_best_tour, mmas_construct, mmas_create,
+from .mmas import (Batch, Colony, MMASError, load, mmas_best_tour, mmas_construct, mmas_create,
                    mmas_default_params, mmas_destroy, mmas_get_pheromone, mmas_get_setup,
                    mmas_get_tours, mmas_iterate, mmas_last_error, mmas_set_iteration,
                    mmas_set_pheromone, mmas_stats, mmas_synchronize, mmas_update)
 
-__all__ = ["Colony", "MMASError", "instances", "load", "mmas_best_tour", "mmas_construct",
+__all__ = ["Batch", "Colony", "MMASError", "instances", "load", "mmas_best_tour", "mmas_construct",
            "mmas_create", "mmas_default_params", "mmas_destroy", "mmas_get_pheromone",
            "mmas_get_setup", "mmas_get_tours", "mmas_iterate", "mmas_last_error",
            "mmas_set_iteration", "mmas_set_pheromone", "mmas_stats", "mmas_synchronize",

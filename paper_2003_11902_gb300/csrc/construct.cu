@@ -33,41 +33,67 @@ constexpr uint32_t BULK_CHUNK = 32768u;
 
 enum { CAND = 0, ROW = 1 };
 
-// Bitmask tabu (Sec. 4.1, "BT"): mark / is_visited in O(1).
-template <bool REGMASK>
+// Bitmask tabu (Sec. 4.1, "BT"): mark / is_visited in O(1).  TW = 1, 2 or 4:
+// the bitmask lives in registers, lane l holding words l, l + 32, ... (n up to
+// 1024 TW nodes); TW = 0: in the warp's slice of shared memory.
+template <int TW>
 struct Tabu {
-    uint32_t reg = 0;          // REGMASK: word `lane` of the bitmask
-    uint32_t *w = nullptr;     // otherwise: this warp's words in shared memory
+    static constexpr int R = TW > 0 ? TW : 1;
+    uint32_t reg[R];           // TW > 0: words lane, lane + 32, ...
+    uint32_t *w = nullptr;     // TW = 0: this warp's words in shared memory
     int nw = 0;
 
     __device__ __forceinline__ void clear(int lane)
     {
-        if constexpr (REGMASK) {
-            reg = 0;
+        if constexpr (TW > 0) {
+#pragma unroll
+            for (int j = 0; j < R; ++j) reg[j] = 0;
         } else {
             for (int q = lane; q < nw; q += 32) w[q] = 0;
             __syncwarp();
         }
     }
-    __device__ __forceinline__ void mark(int lane, int v)
+    // Mark node v when `on` (warp-uniform).  Registers: selects, not a branch
+    // (a one-lane branch diverges the warp).
+    __device__ __forceinline__ void mark_if(int lane, int v, bool on)
     {
-        if constexpr (REGMASK) {
-            // select, not a branch: a one-lane branch diverges the warp
-            reg |= ((v >> 5) == lane) ? (1u << (v & 31)) : 0u;
+        if constexpr (TW > 0) {
+            const int q = v >> 5;
+#pragma unroll
+            for (int j = 0; j < R; ++j) reg[j] |= (on && q == lane + 32 * j) ? (1u << (v & 31)) : 0u;
         } else {
-            if (lane == 0) w[v >> 5] |= 1u << (v & 31);
-            __syncwarp();
+            if (on) {
+                if (lane == 0) w[v >> 5] |= 1u << (v & 31);
+                __syncwarp();
+            }
         }
     }
+    __device__ __forceinline__ void mark(int lane, int v) { mark_if(lane, v, true); }
     // The bitmask word that holds node v.  Every lane of the warp must call it.
     __device__ __forceinline__ uint32_t word_of(int v) const
     {
-        if constexpr (REGMASK)
-            return __shfl_sync(FULL, reg, (v >> 5) & 31);
-        else
+        if constexpr (TW == 0) {
             return w[v >> 5];
+        } else if constexpr (TW == 1) {
+            return __shfl_sync(FULL, reg[0], (v >> 5) & 31);
+        } else {
+            const int src = (v >> 5) & 31, j = (v >> 10) & (TW - 1);
+            uint32_t x[R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) x[i] = __shfl_sync(FULL, reg[i], src);
+            uint32_t r = x[0];
+#pragma unroll
+            for (int i = 1; i < R; ++i) r = j == i ? x[i] : r;
+            return r;
+        }
     }
 };
+
+// Register words per lane for an n-node tabu, 0 when it must live in shared memory.
+__host__ __device__ __forceinline__ int tabu_words(int n)
+{
+    return n <= 1024 ? 1 : (n <= 2048 ? 2 : (n <= 4096 ? 4 : 0));
+}
 
 __device__ __forceinline__ uint32_t pick_word(const uint4 &r, int e)
 {
@@ -85,11 +111,10 @@ __device__ __forceinline__ float pick_f(const float4 &r, int e)
 // r from the whole-row stream, with `row` holding the reciprocal weights (RECIP)
 // or the weights.  Eight chunk-columns (1024 nodes) are loaded before use, so
 // rows of up to 1024 nodes cost one memory round trip.
-template <bool REGMASK, bool GREEDY, bool RECIP>
-__device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, uint32_t reg,
-                                        const uint32_t *w, int lane, uint32_t t, uint32_t ant,
-                                        uint32_t it, uint32_t k0, uint32_t k1, uint32_t *err,
-                                        int cur)
+template <int TW, bool GREEDY, bool RECIP>
+__device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, const Tabu<TW> &tb,
+                                        int lane, uint32_t t, uint32_t ant, uint32_t it,
+                                        uint32_t k0, uint32_t k1, uint32_t *err, int cur)
 {
     constexpr int U = 8;
     const int nch = (n + 3) >> 2;
@@ -102,11 +127,7 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, ui
             const int c = c0 + 32 * u + lane;
             const int v0 = c << 2;
             const int vq = v0 < n ? v0 : n - 1;
-            uint32_t word;
-            if constexpr (REGMASK)
-                word = __shfl_sync(FULL, reg, (vq >> 5) & 31);
-            else
-                word = w[vq >> 5];
+            const uint32_t word = tb.word_of(vq);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
             w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0)
                             : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -154,20 +175,19 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, ui
 // trip: on clustered instances most fallbacks come early in the tour, with
 // thousands of nodes unvisited, where gathering only the unvisited entries
 // costs many more round trips.
-template <bool REGMASK>
-__device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, uint32_t reg,
-                                          const uint32_t *w, int lane, int mode, uint32_t t,
-                                          uint32_t ant, uint32_t it, uint32_t k0, uint32_t k1,
-                                          uint32_t *err, int cur)
+template <int TW>
+__device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, const Tabu<TW> tb,
+                                          int lane, int mode, uint32_t t, uint32_t ant, uint32_t it,
+                                          uint32_t k0, uint32_t k1, uint32_t *err, int cur)
 {
-    if (mode == 0) return scan_row<REGMASK, true, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
-    return scan_row<REGMASK, false, false>(row, n, reg, w, lane, t, ant, it, k0, k1, err, cur);
+    if (mode == 0) return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
+    return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
 }
 
 // One candidate-list step: lane c scores slot c of cur's list.
-template <bool REGMASK>
+template <int TW>
 __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t *cc,
-                                         const float *cw, const Tabu<REGMASK> &tb, int lane,
+                                         const float *cw, const Tabu<TW> &tb, int lane,
                                          int cur, float lg, int t, int ant, uint32_t it,
                                          uint32_t &fbn)
 {
@@ -185,8 +205,8 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     const uint32_t mx = __reduce_max_sync(FULL, k);
     if (__builtin_expect(mx != 0u, 1)) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
     ++fbn;
-    return cand_fallback<REGMASK>(a.wmat + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane, a.fallback,
-                                  (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur);
+    return cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
+                             (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur);
 }
 
 // Store the window of steps [32w, t_end]: lane l holds entry 32w + l.
@@ -199,9 +219,9 @@ __device__ __forceinline__ void store_window(int32_t *trow, int lane, int w, int
 // of group g+1 runs in slices and its log2s replace lg.  CHECK: skip t == 0 and
 // t >= n and store windows here (first and last groups); otherwise the caller
 // stores the window after every eighth group.
-template <bool CHECK, bool REGMASK>
+template <bool CHECK, int TW>
 __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_t *cc,
-                                           const float *cw, Tabu<REGMASK> &tb, int32_t *trow,
+                                           const float *cw, Tabu<TW> &tb, int32_t *trow,
                                            int lane, int ant, uint32_t it, int g, float (&lg)[4],
                                            int &cur, int &twin, uint32_t &fbn)
 {
@@ -223,7 +243,7 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
         }
         const int t = 4 * g + j;
         if (CHECK && (t == 0 || t >= a.n)) continue;
-        const int next = cand_step<REGMASK>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
+        const int next = cand_step<TW>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
         tb.mark(lane, next);
         twin = (lane == tb32 + j) ? next : twin;
         if (CHECK && ((t & 31) == 31 || t == a.n - 1)) store_window(trow, lane, t >> 5, t, twin);
@@ -240,9 +260,9 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
 // interleave.  Only a frozen group leaves the block: that step takes the
 // out-of-line fallback and the group's remaining steps run one by one.  The
 // result equals cand_group's step for step.
-template <bool REGMASK>
+template <int TW>
 __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const uint16_t *cc,
-                                                const float *cw, Tabu<REGMASK> &tb, int lane,
+                                                const float *cw, Tabu<TW> &tb, int lane,
                                                 int ant, uint32_t it, int g, float (&lg)[4],
                                                 int &cur, int &twin, uint32_t &fbn)
 {
@@ -275,11 +295,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         const uint32_t nxt = __reduce_min_sync(FULL, (k == mx && mx != 0u) ? v : 0xFFFFFFFFu);
         jfail = (live && mx == 0u) ? j : jfail;
         live = live && mx != 0u;
-        if constexpr (REGMASK) {
-            tb.reg |= (live && (int)(nxt >> 5) == lane) ? (1u << (nxt & 31)) : 0u;
-        } else {
-            if (live) tb.mark(lane, (int)nxt);
-        }
+        tb.mark_if(lane, (int)nxt, live);
         twin = (live && lane == tb32 + j) ? (int)nxt : twin;
         cur = live ? (int)nxt : cur;
     }
@@ -287,16 +303,16 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         // step 4g + jfail: every candidate of cur is visited
         ++fbn;
         const int t = 4 * g + jfail;
-        const int fb = cand_fallback<REGMASK>(a.wmat + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane,
-                                              a.fallback, (uint32_t)t, (uint32_t)ant, it, a.key0,
-                                              a.key1, &a.sc->err, cur);
+        const int fb = cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
+                                         (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
+                                         cur);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
         cur = fb;
 #pragma unroll
         for (int j = 1; j < 4; ++j) {
             if (j <= jfail) continue;
-            const int next = cand_step<REGMASK>(a, cc, cw, tb, lane, cur, lg[j], 4 * g + j, ant,
+            const int next = cand_step<TW>(a, cc, cw, tb, lane, cur, lg[j], 4 * g + j, ant,
                                                 it, fbn);
             tb.mark(lane, next);
             twin = (lane == tb32 + j) ? next : twin;
@@ -307,7 +323,89 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
     for (int j = 0; j < 4; ++j) lg[j] = nl[j];
 }
 
-template <int MODE, bool STAGED, bool REGMASK>
+// Build the tour of ant `ant` (its global index, which keys the draws) into
+// trow: a uniform start (Alg. 1), then n - 1 selections.  `it` is the
+// iteration index; cc / cw are the candidate table (staged or global) or the
+// reciprocal weight matrix (whole-row mode).
+template <int MODE, int TW>
+__device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_t *cc,
+                                           const float *cw, Tabu<TW> &tb, int lane, int ant,
+                                           uint32_t it, int32_t *trow)
+{
+    // Alg. 1: the first node is drawn uniformly
+    uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
+    philox_rounds<0, 10>(s4, a.key0, a.key1);
+    const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
+    tb.clear(lane);
+    tb.mark(lane, start);
+    int cur = start;
+    int twin = start;  // lane l holds entry 32w + l of the current window
+    uint32_t fbn = 0;
+
+    if constexpr (MODE == CAND) {
+        float lg[4];
+        {
+            uint4 r = make_uint4((uint32_t)lane, 0u, (uint32_t)ant, it);
+            philox_rounds<0, 10>(r, a.key0, a.key1);
+            lg[0] = 0.0f;  // step 0 is the start node
+            lg[1] = log2f(unit_open(r.y));
+            lg[2] = log2f(unit_open(r.z));
+            lg[3] = log2f(unit_open(r.w));
+        }
+        cand_group<true, TW>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
+        int g = 1;
+        for (; 4 * g + 3 <= a.n - 1; ++g) {
+            cand_group_spec<TW>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
+            if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
+        }
+        if (4 * g <= a.n - 1)
+            cand_group<true, TW>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
+        else if (g > 1 && ((g - 1) & 7) != 7)
+            store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
+    } else {
+        for (int t = 1; t < a.n; ++t) {
+            const int next = scan_row<TW, false, true>(cw + (size_t)cur * a.ld, a.n, tb, lane,
+                                                       (uint32_t)t, (uint32_t)ant, it, a.key0,
+                                                       a.key1, &a.sc->err, cur);
+            tb.mark(lane, next);
+            twin = (lane == (t & 31)) ? next : twin;
+            if ((t & 31) == 31 || t == a.n - 1) store_window(trow, lane, t >> 5, t, twin);
+            cur = next;
+        }
+    }
+    if (lane == 0 && fbn) atomicAdd(&a.sc->fallback_steps, (unsigned long long)fbn);
+}
+
+// Stage `bytes_w` bytes of weights and `bytes_c` of ids into shared memory
+// with the bulk-copy engine (thread 0 issues, every thread waits on the
+// mbarrier, bounded).  Returns false on a timeout, after which the CTA must
+// not use the table.  `parity` is the mbarrier phase this copy completes.
+__device__ __forceinline__ bool stage_table(unsigned char *s_w, const void *src_w, uint32_t bytes_w,
+                                            unsigned char *s_c, const void *src_c, uint32_t bytes_c,
+                                            uint64_t *bar, uint32_t parity, uint32_t *err)
+{
+    if (threadIdx.x == 0) {
+        // the table's shared memory may have been read by this CTA's threads
+        // (generic proxy) before the bulk copy (async proxy) overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, bytes_w + bytes_c);
+        const unsigned char *sw = static_cast<const unsigned char *>(src_w);
+        for (uint32_t o = 0; o < bytes_w; o += BULK_CHUNK)
+            bulk_copy_g2s(s_w + o, sw + o, min(BULK_CHUNK, bytes_w - o), bar);
+        const unsigned char *sc = static_cast<const unsigned char *>(src_c);
+        for (uint32_t o = 0; o < bytes_c; o += BULK_CHUNK)
+            bulk_copy_g2s(s_c + o, sc + o, min(BULK_CHUNK, bytes_c - o), bar);
+    }
+    if (!mbar_wait_bounded(bar, parity, STAGE_LIMIT_NS)) {
+        if (threadIdx.x == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
+        // let copies still in flight land before the CTA's memory is released
+        mbar_wait_bounded(bar, parity, STAGE_LIMIT_NS);
+        return false;
+    }
+    return true;
+}
+
+template <int MODE, bool STAGED, int TW>
 __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -326,28 +424,16 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
         off += 16;
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(bar, a.stage_w_bytes + a.stage_c_bytes);
-            const unsigned char *src_w = reinterpret_cast<const unsigned char *>(cw);
-            for (uint32_t o = 0; o < a.stage_w_bytes; o += BULK_CHUNK)
-                bulk_copy_g2s(s_w + o, src_w + o, min(BULK_CHUNK, a.stage_w_bytes - o), bar);
-            const unsigned char *src_c = reinterpret_cast<const unsigned char *>(a.cand16);
-            for (uint32_t o = 0; o < a.stage_c_bytes; o += BULK_CHUNK)
-                bulk_copy_g2s(s_c + o, src_c + o, min(BULK_CHUNK, a.stage_c_bytes - o), bar);
-        }
-        if (!mbar_wait_bounded(bar, 0, STAGE_LIMIT_NS)) {
-            if (threadIdx.x == 0) atomicOr(&a.sc->err, ERR_STAGE_TIMEOUT);
-            // let copies still in flight land before the CTA's memory is released
-            mbar_wait_bounded(bar, 0, STAGE_LIMIT_NS);
+        if (!stage_table(s_w, cw, a.stage_w_bytes, s_c, a.cand16, a.stage_c_bytes, bar, 0,
+                         &a.sc->err))
             return;
-        }
         cw = reinterpret_cast<const float *>(s_w);
         cc = reinterpret_cast<const uint16_t *>(s_c);
     }
 
-    Tabu<REGMASK> tb;
+    Tabu<TW> tb;
     tb.nw = (a.n + 31) >> 5;
-    if constexpr (!REGMASK) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
+    if constexpr (TW == 0) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
 
     const int stride = gridDim.x * cons_warps;
     // `ant` is the global ant index (it keys the draws); this colony's tour rows
@@ -355,64 +441,101 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     // by ant_offset rows (one induction variable keeps the step loop lean)
     const int ant_end = a.ant_offset + a.m;
     int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
-    for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride) {
-        // Alg. 1: the first node is drawn uniformly
-        uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
-        philox_rounds<0, 10>(s4, a.key0, a.key1);
-        const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
-        tb.clear(lane);
-        tb.mark(lane, start);
-        int cur = start;
-        int twin = start;  // lane l holds entry 32w + l of the current window
-        uint32_t fbn = 0;
-        int32_t *trow = tours_g + (size_t)ant * a.ld;
+    for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride)
+        build_tour<MODE, TW>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
+}
 
-        if constexpr (MODE == CAND) {
-            float lg[4];
-            {
-                uint4 r = make_uint4((uint32_t)lane, 0u, (uint32_t)ant, it);
-                philox_rounds<0, 10>(r, a.key0, a.key1);
-                lg[0] = 0.0f;  // step 0 is the start node
-                lg[1] = log2f(unit_open(r.y));
-                lg[2] = log2f(unit_open(r.z));
-                lg[3] = log2f(unit_open(r.w));
-            }
-            cand_group<true, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
-            int g = 1;
-            for (; 4 * g + 3 <= a.n - 1; ++g) {
-                cand_group_spec<REGMASK>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
-                if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
-            }
-            if (4 * g <= a.n - 1)
-                cand_group<true, REGMASK>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
-            else if (g > 1 && ((g - 1) & 7) != 7)
-                store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
-        } else {
-            for (int t = 1; t < a.n; ++t) {
-                const int next = scan_row<REGMASK, false, true>(
-                    cw + (size_t)cur * a.ld, a.n, tb.reg, tb.w, lane, (uint32_t)t, (uint32_t)ant,
-                    it, a.key0, a.key1, &a.sc->err, cur);
-                tb.mark(lane, next);
-                twin = (lane == (t & 31)) ? next : twin;
-                if ((t & 31) == 31 || t == a.n - 1) store_window(trow, lane, t >> 5, t, twin);
-                cur = next;
-            }
+// Batched construction (NEXT-2): one persistent launch builds every ant of
+// every colony.  A CTA repeatedly takes the next chunk (one colony, up to one
+// ant per warp) from a global counter -- the chunk list is ordered by
+// decreasing n so the longest tours start first -- loads that colony's
+// arguments, stages its candidate table when table and tabus fit in
+// `smem_bytes`, and builds the chunk's tours.  Candidate-list mode only.
+template <int TW, bool STAGED>
+__device__ __forceinline__ void batch_chunk(const ConstructArgs &a, unsigned char *smem,
+                                            uint64_t *bar, uint32_t &parity, int first, int count,
+                                            int lane, int warp)
+{
+    const uint32_t it = (uint32_t)a.iter[0];
+    const uint16_t *cc = a.cand16;
+    const float *cw = a.cwinv;
+    size_t off = 0;
+    if constexpr (STAGED) {
+        const bool ok = stage_table(smem, a.cwinv, a.stage_w_bytes, smem + a.stage_w_bytes, a.cand16,
+                                    a.stage_c_bytes, bar, parity, &a.sc->err);
+        parity ^= 1u;
+        if (!ok) return;
+        cw = reinterpret_cast<const float *>(smem);
+        cc = reinterpret_cast<const uint16_t *>(smem + a.stage_w_bytes);
+        off = (size_t)a.stage_w_bytes + a.stage_c_bytes;
+    }
+    if (warp >= count) return;
+    Tabu<TW> tb;
+    tb.nw = (a.n + 31) >> 5;
+    if constexpr (TW == 0) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
+    const int ant = first + warp;  // this colony's ant index (ant_offset = 0)
+    build_tour<CAND, TW>(a, cc, cw, tb, lane, ant, it, a.tours + (size_t)ant * a.ld);
+}
+
+__global__ void __launch_bounds__(384, 1)
+    k_construct_batch(const ConstructArgs *__restrict__ args, const BatchChunk *__restrict__ chunks,
+                      int nchunks, unsigned *counter, uint32_t smem_bytes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(16) ConstructArgs s_a;
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_chunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t parity = 0;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    for (;;) {
+        __syncthreads();  // the previous chunk is done with s_a and the table
+        if (threadIdx.x == 0) s_chunk = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int ci = s_chunk;
+        if (ci >= nchunks) break;
+        const BatchChunk ch = chunks[ci];
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(args + ch.colony);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&s_a);
+            for (int i = threadIdx.x; i < (int)(sizeof(ConstructArgs) / 4); i += blockDim.x)
+                dst[i] = src[i];
         }
-        if (lane == 0 && fbn) atomicAdd(&a.sc->fallback_steps, (unsigned long long)fbn);
+        __syncthreads();
+        const ConstructArgs &a = s_a;
+        const int tw = tabu_words(a.n);
+        const size_t masks = tw ? 0 : (size_t)nwarps * ((a.n + 31) >> 5) * sizeof(uint32_t);
+        const bool staged = (size_t)a.stage_w_bytes + a.stage_c_bytes + masks <= smem_bytes;
+#define MMAS_BATCH_CHUNK(TWV)                                                                   \
+    do {                                                                                        \
+        if (staged)                                                                             \
+            batch_chunk<TWV, true>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);    \
+        else                                                                                    \
+            batch_chunk<TWV, false>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);   \
+    } while (0)
+        if (tw == 1) MMAS_BATCH_CHUNK(1);
+        else if (tw == 2) MMAS_BATCH_CHUNK(2);
+        else if (tw == 4) MMAS_BATCH_CHUNK(4);
+        else MMAS_BATCH_CHUNK(0);
+#undef MMAS_BATCH_CHUNK
     }
 }
 
 using KernelFn = void (*)(const ConstructArgs, int);
 
-KernelFn pick_kernel(int mode, int staged, int regmask)
+// tw: tabu words per lane (1, 2, 4), or 0 for the shared-memory tabu
+KernelFn pick_kernel(int mode, int staged, int tw)
 {
-    static const KernelFn table[8] = {
-        k_construct<CAND, false, false>, k_construct<CAND, false, true>,
-        k_construct<CAND, true, false>,  k_construct<CAND, true, true>,
-        k_construct<ROW, false, false>,  k_construct<ROW, false, true>,
-        k_construct<ROW, true, false>,   k_construct<ROW, true, true>,
+    static const KernelFn table[16] = {
+        k_construct<CAND, false, 0>, k_construct<CAND, false, 1>, k_construct<CAND, false, 2>,
+        k_construct<CAND, false, 4>, k_construct<CAND, true, 0>,  k_construct<CAND, true, 1>,
+        k_construct<CAND, true, 2>,  k_construct<CAND, true, 4>,  k_construct<ROW, false, 0>,
+        k_construct<ROW, false, 1>,  k_construct<ROW, false, 2>,  k_construct<ROW, false, 4>,
+        k_construct<ROW, true, 0>,   k_construct<ROW, true, 1>,   k_construct<ROW, true, 2>,
+        k_construct<ROW, true, 4>,
     };
-    return table[(mode << 2) | (staged << 1) | regmask];
+    const int ti = tw == 4 ? 3 : tw;  // 0, 1, 2, 4 -> 0, 1, 2, 3
+    return table[(mode << 3) | (staged << 2) | ti];
 }
 
 }  // namespace
@@ -422,14 +545,14 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
 {
     const bool row = a.cl == 0;
     const int nw = (a.n + 31) / 32;
-    plan->regmask = a.n <= 1024;
+    plan->tw = tabu_words(a.n);
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
     // staged: one CTA per SM (the table fills its shared memory) carrying
     // ceil(m / #SMs) ants, at most 12 warps; warps loop over further ants
     int w = (a.m + num_sms - 1) / num_sms;
     w = w < 1 ? 1 : (w > 12 ? 12 : w);
-    const size_t masks = plan->regmask ? 0 : (size_t)w * nw * sizeof(uint32_t);
+    const size_t masks = plan->tw ? 0 : (size_t)w * nw * sizeof(uint32_t);
     const size_t need = table + 16 + masks;
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
@@ -443,11 +566,26 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->cons_warps = 4;
         plan->gen_warps = 0;
         plan->grid = (a.m + 3) / 4;
-        plan->smem = plan->regmask ? 0 : (size_t)4 * nw * sizeof(uint32_t);
+        plan->smem = plan->tw ? 0 : (size_t)4 * nw * sizeof(uint32_t);
     }
-    KernelFn k = pick_kernel(row ? ROW : CAND, plan->staged, plan->regmask);
+    KernelFn k = pick_kernel(row ? ROW : CAND, plan->staged, plan->tw);
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+}
+
+cudaError_t prepare_construct_batch(size_t smem_bytes)
+{
+    return cudaFuncSetAttribute(reinterpret_cast<const void *>(k_construct_batch),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+cudaError_t launch_construct_batch(const ConstructArgs *args, const BatchChunk *chunks, int nchunks,
+                                   unsigned *counter, int grid, int warps, size_t smem_bytes,
+                                   cudaStream_t s)
+{
+    k_construct_batch<<<grid, warps * 32, smem_bytes, s>>>(args, chunks, nchunks, counter,
+                                                           (uint32_t)smem_bytes);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s)
@@ -460,7 +598,7 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
         b.stage_w_bytes = (uint32_t)((size_t)a.n * a.ld * sizeof(float));
         b.stage_c_bytes = 0;
     }
-    KernelFn k = pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.regmask);
+    KernelFn k = pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw);
     k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();
 }

@@ -1,0 +1,52 @@
+// The single-colony handle behind the C ABI, shared by the runtime and the
+// batched-colony front end.
+#pragma once
+
+#include <string>
+
+#include "internal.cuh"
+#include "mmas.h"
+#include "twoopt.cuh"
+
+struct mmas_handle {
+    int device = 0;
+    int n = 0, m = 0, cl = 0, ld = 0;
+    mmas_params p{};
+    double p_root = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+
+    int2 *xy = nullptr;
+    int32_t *dist = nullptr;
+    float *eb = nullptr, *tau = nullptr, *wmat = nullptr, *cwinv = nullptr;
+    int32_t *cand32 = nullptr;
+    uint16_t *cand16 = nullptr;
+    int32_t *tours = nullptr, *lens = nullptr, *gb_tour = nullptr, *nn_tour = nullptr;
+    int2 *nbr = nullptr;
+    mmas::Scalars *sc = nullptr;
+    int *maxd = nullptr;
+    int32_t *ext_tour = nullptr, *ext_len = nullptr;
+    int32_t *nnd = nullptr;
+    mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
+
+    mmas::ConstructArgs cargs{};
+    mmas::ConstructPlan cplan{};
+    mmas::BestArgs bargs{};
+    mmas::ScoreArgs sargs{};
+    mmas::TwoOptArgs targs{};
+    mmas::UpdateArgs uargs{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool timing = false;
+    bool timed_run = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::string err;
+};
+
+namespace mmas {
+// Host-side checks of one colony's instance and parameters (no device work);
+// on failure the message is the calling thread's mmas_last_error(NULL).
+mmas_status validate_colony(const mmas_instance *inst, const mmas_params *params);
+}  // namespace mmas

@@ -197,9 +197,14 @@ struct ConstructArgs {
     uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
 };
 
+// One unit of batched construction: ants first .. first+count-1 of a colony.
+struct BatchChunk {
+    int32_t colony, first, count;
+};
+
 struct ConstructPlan {
     int staged;     // stage the weight (and id) tables in shared memory
-    int regmask;    // tabu bitmask held in registers (n <= 1024)
+    int tw;         // tabu words per lane in registers (1, 2, 4; n <= 1024 tw), 0: shared memory
     int cons_warps; // warps building tours (one ant each) per CTA
     int gen_warps;  // reserved (0)
     int grid;
@@ -260,9 +265,17 @@ cudaError_t launch_init_colony(int32_t n, int32_t ld, double rho, double p_root,
 cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
                            ConstructPlan *plan);
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s);
+cudaError_t prepare_construct_batch(size_t smem_bytes);
+cudaError_t launch_construct_batch(const ConstructArgs *args, const BatchChunk *chunks, int nchunks,
+                                   unsigned *counter, int grid, int warps, size_t smem_bytes,
+                                   cudaStream_t s);
 
 cudaError_t launch_best(const BestArgs &a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_score_batch(const ScoreArgs *args, const int32_t *ant_colony, const int32_t *ant_base,
+                               int total_ants, bool xy, cudaStream_t s);
+cudaError_t launch_update_batch(const UpdateArgs *args, const int32_t *row_colony, const int32_t *row_base,
+                                int total_rows, bool alpha1, cudaStream_t s);
 
 }  // namespace mmas

@@ -95,50 +95,56 @@ __device__ void select_best(const BestArgs &a)
 
 __global__ void __launch_bounds__(1024) k_best(const BestArgs a) { select_best(a); }
 
+// Length of one tour, summed by the whole CTA (the result is valid in thread
+// 0).  Each thread takes four consecutive edges per round (an int4 of the tour
+// plus the following node) and issues all of their loads before using them.
+// Distances are the exact integer ones.
+template <bool XY>
+__device__ __forceinline__ int score_ant(const ScoreArgs &a, int ant, int *red)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t *tr = a.tours + (size_t)ant * a.ld;
+    int part = 0;
+    for (int q = tid; 4 * q < a.n; q += blockDim.x) {
+        const int t0 = 4 * q;
+        const int4 u4 = *reinterpret_cast<const int4 *>(tr + t0);  // ld is a multiple of 32
+        const int nx = tr[t0 + 4 < a.n ? t0 + 4 : 0];
+        const int node[5] = {u4.x, u4.y, u4.z, u4.w, nx};
+        const int cnt = a.n - t0 < 4 ? a.n - t0 : 4;  // edges t0 .. t0+cnt-1
+        // edge e joins node[e] and node[e+1]; the last real edge closes on nx
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= cnt) break;
+            const int from = node[e];
+            const int to = (e + 1 < cnt) ? node[e + 1] : nx;
+            if constexpr (XY)
+                part += euc2d_exact(__ldg(a.xy + from), __ldg(a.xy + to));
+            else
+                part += __ldg(a.dist + (size_t)from * a.ld + to);
+        }
+    }
+    part = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    int sum = 0;
+    if (tid == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
+    __syncthreads();
+    return sum;
+}
+
 // Tour lengths, then -- when a.best -- the last CTA to finish runs select_best
-// on all m lengths.  One CTA per ant; each thread takes four consecutive edges
-// per round (an int4 of the tour plus the following node) and issues all of
-// their loads before using them.  Distances are the exact integer ones.
+// on all m lengths.  One CTA per ant (looping when m exceeds the grid).
 template <bool XY>
 __global__ void __launch_bounds__(256) k_score(const ScoreArgs a)
 {
     __shared__ int red[8];
     __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int acc = 0;
+    const int tid = threadIdx.x;
     for (int ant = blockIdx.x; ant < a.m; ant += gridDim.x) {
-        const int32_t *tr = a.tours + (size_t)ant * a.ld;
-        int part = 0;
-        for (int q = tid; 4 * q < a.n; q += blockDim.x) {
-            const int t0 = 4 * q;
-            const int4 u4 = *reinterpret_cast<const int4 *>(tr + t0);  // ld is a multiple of 32
-            const int nx = tr[t0 + 4 < a.n ? t0 + 4 : 0];
-            const int node[5] = {u4.x, u4.y, u4.z, u4.w, nx};
-            const int cnt = a.n - t0 < 4 ? a.n - t0 : 4;  // edges t0 .. t0+cnt-1
-            // edge e joins node[e] and node[e+1]; the last real edge closes on nx
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (e >= cnt) break;
-                const int from = node[e];
-                const int to = (e + 1 < cnt) ? node[e + 1] : nx;
-                if constexpr (XY)
-                    part += euc2d_exact(__ldg(a.xy + from), __ldg(a.xy + to));
-                else
-                    part += __ldg(a.dist + (size_t)from * a.ld + to);
-            }
-        }
-        part = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)part);
-        if (lane == 0) red[warp] = part;
-        __syncthreads();
-        if (tid == 0) {
-            int sum = 0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sum += red[i];
-            a.lens[ant] = sum;
-        }
-        __syncthreads();
-        acc += part;
+        const int len = score_ant<XY>(a, ant, red);
+        if (tid == 0) a.lens[ant] = len;
     }
-    (void)acc;
     if (!a.best) return;
     __threadfence();
     __syncthreads();
@@ -150,57 +156,101 @@ __global__ void __launch_bounds__(256) k_score(const ScoreArgs a)
     if (tid == 0) a.b.sc->done = 0;
 }
 
+// Batched lengths (NEXT-2): one CTA per ant of every colony; the last CTA of a
+// colony to finish runs that colony's select_best.
+template <bool XY>
+__global__ void __launch_bounds__(256)
+    k_score_batch(const ScoreArgs *__restrict__ args, const int32_t *__restrict__ ant_colony,
+                  const int32_t *__restrict__ ant_base)
+{
+    __shared__ int red[8];
+    __shared__ int s_last;
+    const int tid = threadIdx.x;
+    const int b = ant_colony[blockIdx.x];
+    const ScoreArgs a = args[b];
+    const int ant = (int)blockIdx.x - ant_base[b];
+    const int len = score_ant<XY>(a, ant, red);
+    if (tid == 0) a.lens[ant] = len;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.b.sc->done, 1u) == (unsigned)a.m - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    select_best(a.b);
+    if (tid == 0) a.b.sc->done = 0;
+}
+
+// Row i of the fused pass: evaporate with both clamps, deposit on the row's
+// two tour edges, write choice_info (or its reciprocal), then gather
+// 1/choice_info of the row's candidates.  The whole CTA works on the row.
+template <bool FULLROW, bool ALPHA1>
+__device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmin, float tmax,
+                                           float delta)
+{
+    const int nq = a.ld >> 2;
+    int succ = -1, pred = -1;
+    if (a.nbr) {
+        const int2 nb = a.nbr[i];
+        succ = nb.x;
+        pred = nb.y;
+    }
+    float4 *trow = reinterpret_cast<float4 *>(a.tau + (size_t)i * a.ld);
+    const float4 *erow = reinterpret_cast<const float4 *>(a.eb + (size_t)i * a.ld);
+    float4 *wrow = reinterpret_cast<float4 *>(a.wmat + (size_t)i * a.ld);
+#pragma unroll 2
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const float4 t4 = trow[q];
+        const float4 e4 = __ldg(erow + q);
+        float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+        const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+        float wv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = (q << 2) + c;
+            float x = tv[c];
+            if (j < a.n) {
+                if (a.evaporate) {
+                    x = fminf(fmaxf(__fmul_rn(x, a.persist), tmin), tmax);
+                    if (j == succ || j == pred) x = fminf(__fadd_rn(x, delta), tmax);
+                }
+                const float w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
+                wv[c] = FULLROW ? __frcp_rn(w) : w;
+            } else {
+                x = 0.0f;
+                wv[c] = 0.0f;
+            }
+            tv[c] = x;
+        }
+        trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+        wrow[q] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    if (!FULLROW && a.cl > 0) {
+        __syncthreads();  // this row's choice_info is written and visible to the CTA
+        const float *w1 = a.wmat + (size_t)i * a.ld;
+        for (int c = threadIdx.x; c < a.cl; c += blockDim.x) {
+            const int v = a.cand32[(size_t)i * a.cl + c];
+            a.cwinv[(size_t)i * a.cl + c] = __frcp_rn(w1[v]);
+        }
+    }
+}
+
 template <bool FULLROW, bool ALPHA1>
 __global__ void __launch_bounds__(256) k_update(const UpdateArgs a)
 {
     const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
-    const int nq = a.ld >> 2;
-    for (int i = blockIdx.x; i < a.n; i += gridDim.x) {
-        int succ = -1, pred = -1;
-        if (a.nbr) {
-            const int2 nb = a.nbr[i];
-            succ = nb.x;
-            pred = nb.y;
-        }
-        float4 *trow = reinterpret_cast<float4 *>(a.tau + (size_t)i * a.ld);
-        const float4 *erow = reinterpret_cast<const float4 *>(a.eb + (size_t)i * a.ld);
-        float4 *wrow = reinterpret_cast<float4 *>(a.wmat + (size_t)i * a.ld);
-#pragma unroll 2
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-            const float4 t4 = trow[q];
-            const float4 e4 = __ldg(erow + q);
-            float tv[4] = {t4.x, t4.y, t4.z, t4.w};
-            const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
-            float wv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = (q << 2) + c;
-                float x = tv[c];
-                if (j < a.n) {
-                    if (a.evaporate) {
-                        x = fminf(fmaxf(__fmul_rn(x, a.persist), tmin), tmax);
-                        if (j == succ || j == pred) x = fminf(__fadd_rn(x, delta), tmax);
-                    }
-                    const float w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
-                    wv[c] = FULLROW ? __frcp_rn(w) : w;
-                } else {
-                    x = 0.0f;
-                    wv[c] = 0.0f;
-                }
-                tv[c] = x;
-            }
-            trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
-            wrow[q] = make_float4(wv[0], wv[1], wv[2], wv[3]);
-        }
-        if (!FULLROW && a.cl > 0) {
-            __syncthreads();  // this row's choice_info is written and visible to the CTA
-            const float *w1 = a.wmat + (size_t)i * a.ld;
-            for (int c = threadIdx.x; c < a.cl; c += blockDim.x) {
-                const int v = a.cand32[(size_t)i * a.cl + c];
-                a.cwinv[(size_t)i * a.cl + c] = __frcp_rn(w1[v]);
-            }
-        }
-    }
+    for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row<FULLROW, ALPHA1>(a, i, tmin, tmax, delta);
+}
+
+// Batched fused pass (NEXT-2): one CTA per row of every colony.
+template <bool ALPHA1>
+__global__ void __launch_bounds__(256)
+    k_update_batch(const UpdateArgs *__restrict__ args, const int32_t *__restrict__ row_colony,
+                   const int32_t *__restrict__ row_base)
+{
+    const int b = row_colony[blockIdx.x];
+    const UpdateArgs a = args[b];
+    update_row<false, ALPHA1>(a, (int)blockIdx.x - row_base[b], a.sc->tmin, a.sc->tmax, a.sc->delta);
 }
 
 }  // namespace
@@ -219,6 +269,26 @@ cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s)
         k_score<true><<<grid, 256, 0, s>>>(a);
     else
         k_score<false><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_batch(const ScoreArgs *args, const int32_t *ant_colony, const int32_t *ant_base,
+                               int total_ants, bool xy, cudaStream_t s)
+{
+    if (xy)
+        k_score_batch<true><<<total_ants, 256, 0, s>>>(args, ant_colony, ant_base);
+    else
+        k_score_batch<false><<<total_ants, 256, 0, s>>>(args, ant_colony, ant_base);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(const UpdateArgs *args, const int32_t *row_colony, const int32_t *row_base,
+                                int total_rows, bool alpha1, cudaStream_t s)
+{
+    if (alpha1)
+        k_update_batch<true><<<total_rows, 256, 0, s>>>(args, row_colony, row_base);
+    else
+        k_update_batch<false><<<total_rows, 256, 0, s>>>(args, row_colony, row_base);
     return cudaGetLastError();
 }
 

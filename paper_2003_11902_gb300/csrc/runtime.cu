@@ -19,48 +19,9 @@
 #include <string>
 #include <vector>
 
-#include "internal.cuh"
-#include "twoopt.cuh"
-#include "mmas.h"
+#include "handle.cuh"
 
 using namespace mmas;
-
-struct mmas_handle {
-    int device = 0;
-    int n = 0, m = 0, cl = 0, ld = 0;
-    mmas_params p{};
-    double p_root = 0.0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int num_sms = 0;
-    size_t smem_optin = 0;
-
-    int2 *xy = nullptr;
-    int32_t *dist = nullptr;
-    float *eb = nullptr, *tau = nullptr, *wmat = nullptr, *cwinv = nullptr;
-    int32_t *cand32 = nullptr;
-    uint16_t *cand16 = nullptr;
-    int32_t *tours = nullptr, *lens = nullptr, *gb_tour = nullptr, *nn_tour = nullptr;
-    int2 *nbr = nullptr;
-    Scalars *sc = nullptr;
-    int *maxd = nullptr;
-    int32_t *ext_tour = nullptr, *ext_len = nullptr;
-    int32_t *nnd = nullptr;
-    Scalars *h_sc = nullptr;  // pinned mirror of *sc
-
-    ConstructArgs cargs{};
-    ConstructPlan cplan{};
-    BestArgs bargs{};
-    ScoreArgs sargs{};
-    TwoOptArgs targs{};
-    UpdateArgs uargs{};
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    bool timing = false;
-    bool timed_run = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    std::string err;
-};
 
 namespace {
 
@@ -372,6 +333,13 @@ mmas_status check_handle(mmas_handle *h)
 }  // namespace
 
 void mmas::set_thread_error(const std::string &msg) { tl_error = msg; }
+
+mmas_status mmas::validate_colony(const mmas_instance *inst, const mmas_params *params)
+{
+    mmas_params p = *params;
+    if (p.m == 0) p.m = inst->n;
+    return validate(inst, &p);
+}
 
 extern "C" {
 

@@ -28,7 +28,12 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
-           "mmas_phase_times", "mmas_score_tours_noalloc"]
+           "mmas_phase_times", "mmas_score_tours_noalloc",
+           "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
+           "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
+           "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
+           "mmas_batch_enable_phase_timing", "mmas_batch_phase_times", "mmas_batch_fallback_steps",
+           "mmas_batch_destroy", "mmas_batch_last_error"]
 MMAS_NOALLOC_MAX_ANTS = 1048576
 
 
@@ -41,6 +46,10 @@ class mmas_params(C.Structure):
                 ("p_best", C.c_float), ("cl", C.c_int32), ("seed", C.c_uint64),
                 ("deposit", C.c_int32), ("fallback", C.c_int32), ("device", C.c_int32),
                 ("ant_offset", C.c_int32), ("ls", C.c_int32), ("stream", C.c_void_p)]
+
+
+class mmas_batch_config(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
 
 
 class mmas_stats_t(C.Structure):
@@ -93,6 +102,20 @@ def load(path: str = LIB_PATH):
             "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
             "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+            "mmas_batch_create": (C.c_int, [P(mmas_instance), i32, P(mmas_params), P(H)]),
+            "mmas_batch_iterate": (C.c_int, [H, i32]),
+            "mmas_batch_best_tour": (C.c_int, [H, i32, P(i32), P(i32)]),
+            "mmas_batch_best_lengths": (C.c_int, [H, P(i32)]),
+            "mmas_batch_get_tours": (C.c_int, [H, i32, P(i32), P(i32)]),
+            "mmas_batch_set_config": (C.c_int, [H, P(mmas_batch_config)]),
+            "mmas_batch_get_config": (C.c_int, [H, P(mmas_batch_config)]),
+            "mmas_batch_autotune": (C.c_int, [H, i32, P(mmas_batch_config)]),
+            "mmas_batch_synchronize": (C.c_int, [H]),
+            "mmas_batch_enable_phase_timing": (C.c_int, [H, i32]),
+            "mmas_batch_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
+            "mmas_batch_fallback_steps": (C.c_int, [H, P(i64)]),
+            "mmas_batch_destroy": (None, [H]),
+            "mmas_batch_last_error": (C.c_char_p, [H]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -332,3 +355,119 @@ class Colony:
 
     def phase_times(self):
         return mmas_phase_times(self._h)
+
+
+# ------------------------------------------------------------------- batches
+
+def _bcheck(b, status):
+    if status != MMAS_OK:
+        msg = load().mmas_batch_last_error(b)
+        raise MMASError(status, msg.decode() if msg else "")
+
+
+def mmas_batch_create(instances, params: mmas_params):
+    """instances: list of (xy or None, dist or None) int32 arrays; returns the handle."""
+    arr = (mmas_instance * len(instances))()
+    keep = []
+    for i, (xy, dist) in enumerate(instances):
+        if (xy is None) == (dist is None):
+            raise ValueError("give exactly one of xy and dist per instance")
+        a = np.ascontiguousarray(xy if xy is not None else dist, dtype=np.int32)
+        keep.append(a)
+        arr[i].n = a.shape[0]
+        if xy is not None:
+            arr[i].xy = _i32p(a)
+        else:
+            arr[i].dist = _i32p(a)
+    b = C.c_void_p()
+    _bcheck(None, load().mmas_batch_create(arr, len(instances), C.byref(params), C.byref(b)))
+    return b
+
+
+class Batch:
+    """Many colonies advanced together (batched launches; see include/mmas.h).
+    Colony c uses seed + c and m = m or n_c."""
+
+    def __init__(self, xys=None, dists=None, m=0, alpha=1.0, beta=2.0, rho=0.02, p_best=0.01,
+                 cl=32, seed=1, deposit=0, fallback=0, device=0, stream="torch"):
+        if (xys is None) == (dists is None):
+            raise ValueError("give exactly one of xys and dists")
+        insts = [(x, None) for x in xys] if xys is not None else [(None, d) for d in dists]
+        p = mmas_default_params()
+        p.m = int(m)
+        p.alpha, p.beta, p.rho, p.p_best = alpha, beta, rho, p_best
+        p.cl, p.seed, p.deposit, p.fallback, p.device = cl, int(seed), deposit, fallback, device
+        if stream == "torch":
+            stream = _torch_stream()
+        elif stream == 0:
+            stream = CUDA_STREAM_LEGACY
+        p.stream = stream
+        self.ns = [np.asarray(x if x is not None else d).shape[0] for x, d in insts]
+        self.ms = [int(m) if m else n for n in self.ns]
+        self._b = mmas_batch_create(insts, p)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().mmas_batch_destroy(self._b)
+            self._b = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.ns)
+
+    def iterate(self, k: int = 1):
+        _bcheck(self._b, load().mmas_batch_iterate(self._b, k))
+
+    def best_tour(self, c: int):
+        tour = np.zeros(self.ns[c], np.int32)
+        length = C.c_int32()
+        _bcheck(self._b, load().mmas_batch_best_tour(self._b, c, _i32p(tour), C.byref(length)))
+        return length.value, tour
+
+    def best_lengths(self):
+        out = np.zeros(len(self.ns), np.int32)
+        _bcheck(self._b, load().mmas_batch_best_lengths(self._b, _i32p(out)))
+        return out
+
+    def tours(self, c: int):
+        t = np.zeros((self.ms[c], self.ns[c]), np.int32)
+        lens = np.zeros(self.ms[c], np.int32)
+        _bcheck(self._b, load().mmas_batch_get_tours(self._b, c, _i32p(t), _i32p(lens)))
+        return t, lens
+
+    def set_config(self, warps_per_cta: int, ctas_per_sm: int):
+        cfg = mmas_batch_config(warps_per_cta, ctas_per_sm)
+        _bcheck(self._b, load().mmas_batch_set_config(self._b, C.byref(cfg)))
+
+    def config(self):
+        cfg = mmas_batch_config()
+        _bcheck(self._b, load().mmas_batch_get_config(self._b, C.byref(cfg)))
+        return cfg.warps_per_cta, cfg.ctas_per_sm
+
+    def autotune(self, reps: int = 3):
+        cfg = mmas_batch_config()
+        _bcheck(self._b, load().mmas_batch_autotune(self._b, reps, C.byref(cfg)))
+        return cfg.warps_per_cta, cfg.ctas_per_sm
+
+    def synchronize(self):
+        _bcheck(self._b, load().mmas_batch_synchronize(self._b))
+
+    def enable_phase_timing(self, enable: bool = True):
+        _bcheck(self._b, load().mmas_batch_enable_phase_timing(self._b, int(enable)))
+
+    def phase_times(self):
+        a, b, t = C.c_float(), C.c_float(), C.c_float()
+        _bcheck(self._b, load().mmas_batch_phase_times(self._b, C.byref(a), C.byref(b), C.byref(t)))
+        return a.value, b.value, t.value
+
+    def fallback_steps(self) -> int:
+        v = C.c_int64()
+        _bcheck(self._b, load().mmas_batch_fallback_steps(self._b, C.byref(v)))
+        return v.value

@@ -26,7 +26,7 @@ def _declared():
 
 def test_every_declared_symbol_is_exported(lib):
     declared = _declared()
-    assert len(declared) == 18
+    assert len(declared) == 32
     assert sorted(mmas.EXPORTS) == declared
     for name in declared:
         assert hasattr(lib, name), name
@@ -37,6 +37,7 @@ def test_struct_layout_matches_header():
     assert mmas.mmas_params.seed.offset == 24
     assert mmas.mmas_params.stream.offset == 56
     assert C.sizeof(mmas.mmas_instance) == 24
+    assert C.sizeof(mmas.mmas_batch_config) == 8
 
 
 def test_default_params(lib):
@@ -96,3 +97,32 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     with pytest.raises(mmas.MMASError) as e:
         mmas.Colony(xy=instances.uniform(20, 1), cl=4, stream=None)
     assert e.value.status == mmas.MMAS_ECUDA
+
+
+@pytest.mark.parametrize("field,value,needle", [
+    ("cl", 0, "1 <= cl <= 32"), ("ls", 1, "local search"), ("ant_offset", 5, "ant_offset"),
+])
+def test_batch_restrictions_are_checked_first(lib, field, value, needle):
+    p = mmas.mmas_default_params()
+    setattr(p, field, value)
+    with pytest.raises(mmas.MMASError) as e:
+        mmas.mmas_batch_create([(instances.uniform(30, 1), None)], p)
+    assert e.value.status == mmas.MMAS_EINVAL and needle in str(e.value)
+    assert needle in load_batch_error(lib)
+
+
+def load_batch_error(lib):
+    return lib.mmas_batch_last_error(None).decode()
+
+
+def test_batch_instance_checks(lib):
+    p = mmas.mmas_default_params()
+    p.cl = 4
+    with pytest.raises(mmas.MMASError, match="every instance"):
+        mmas.mmas_batch_create([(instances.uniform(30, 1), None),
+                                (None, np.zeros((3, 3), np.int32))], p)
+    with pytest.raises(mmas.MMASError, match="count >= 1"):
+        mmas.mmas_batch_create([], p)
+    # colony 0 fails its own validation: the message names it
+    with pytest.raises(mmas.MMASError, match="colony 0: n must be"):
+        mmas.mmas_batch_create([(instances.uniform(2, 1), None), (instances.uniform(30, 2), None)], p)
