@@ -46,7 +46,13 @@ WORKLOADS = {
     "uniform-n1000-cl32": dict(n=1000, m=1000, cl=32, kind="uniform", iseed=1001),
     "uniform-n200-fullrow": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002),
     "clustered-n3800-cl16-2opt": dict(n=3800, m=1000, cl=16, kind="clustered", iseed=1003, ls=1),
+    # 256 uniform instances, n = round(exp(U[ln 100, ln 2000])) (size seed 1000), coordinate
+    # seed 1000 + i, m = n each
+    "batched-256-n100-2000-cl32": dict(kind="batched", count=256, lo=100, hi=2000, cl=32,
+                                       size_seed=1000),
 }
+DEFAULT_STEPS = {"uniform-n1000-cl32": 1000, "uniform-n200-fullrow": 1000,
+                 "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30}
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
 # kernels in one iteration graph: construct, score, update; with 2-opt of the
 # iteration best also the 2-opt and the best/limits kernel; with 2-opt of every
@@ -64,6 +70,19 @@ def _instance(w):
     if w["kind"] == "uniform":
         return I.uniform(w["n"], w["iseed"])
     return I.clustered(w["n"], w["iseed"])
+
+
+def _batch_instances(w):
+    from paper_2003_11902_gb300 import instances as I
+    ns = I.log_uniform_sizes(w["count"], w["size_seed"], w["lo"], w["hi"])
+    return [I.uniform(int(n), 1000 + i) for i, n in enumerate(ns)]
+
+
+def _batch_cfg(w, xys):
+    ns = [len(x) for x in xys]
+    return {"colonies": w["count"], "n": f"log-uniform [{w['lo']}, {w['hi']}]", "n_min": min(ns),
+            "n_max": max(ns), "total_ants": sum(ns), "m": "n per colony", "cl": w["cl"],
+            "instance": "uniform, size seed 1000, coordinate seed 1000 + i", **PARAMS}
 
 
 def _peaks():
@@ -386,10 +405,182 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def cpu_baseline_batch(w, xys, budget_s=12.0):
+    """The oracle as it stands, all host cores: one whole iteration of each colony
+    in turn, from the first, until budget_s."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    tours, done, el = 0, 0, 0.0
+    for b, xy in enumerate(xys):
+        col = O.Colony(xy=xy, m=len(xy), cl=w["cl"], seed=1 + b, **PARAMS)  # set-up, untimed
+        t0 = time.perf_counter()
+        col.iterate(1, threads=cores)
+        el += time.perf_counter() - t0
+        tours += len(xy)
+        done += 1
+        if el >= budget_s:
+            break
+    return {"value": tours / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one whole iteration of each of the first {done} of {len(xys)} colonies "
+                      f"({tours} ants; set-up untimed), OpenMP over ants on {cores} threads, "
+                      f"{el:.1f} s"}
+
+
+def run_reference_batch(args, w):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    xys = _batch_instances(w)
+    cores = os.cpu_count() or 1
+    import oracle as O
+    # each step: whole iterations of colonies taken in turn, bounded to ~budget / steps
+    per_step = 150.0 / (args.steps + args.warmup)
+    cols = {}
+    nxt = 0
+    times, tours = [], 0
+    for step in range(args.warmup + args.steps):
+        el, done = 0.0, 0
+        while el < per_step:
+            b = nxt % len(xys)
+            nxt += 1
+            if b not in cols:  # set-up, untimed
+                cols[b] = O.Colony(xy=xys[b], m=len(xys[b]), cl=w["cl"], seed=1 + b, **PARAMS)
+            t0 = time.perf_counter()
+            cols[b].iterate(1, threads=cores)
+            el += time.perf_counter() - t0
+            done += len(xys[b])
+        if step >= args.warmup:
+            times.append(el)
+            tours += done
+    total = sum(times)
+    value = tours / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, **_batch_cfg(w, xys)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"whole colony iterations taken in turn, ~{per_step:.1f} s "
+                                       f"per step (set-up untimed), {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours_batch(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2003_11902_gb300 import Batch, _build, mmas
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.cuda.current_device()
+    _build.build()
+    xys = _batch_instances(w)
+    ns = [len(x) for x in xys]
+    total_ants = sum(ns)
+    seed = 1 + rank * w["count"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    bt = Batch(xys=xys, m=0, cl=w["cl"], seed=seed, device=dev, stream=stream.cuda_stream,
+               **PARAMS)
+    tuned = bt.autotune(reps=3)
+    bt.enable_phase_timing(True)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        bt.iterate(1)
+    bt.synchronize()
+    fb0 = bt.fallback_steps()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev) if rank == 0 else None
+    con, tot = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        bt.iterate(1)
+        c, _, t = bt.phase_times()
+        con.append(c)
+        tot.append(t)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop() if sampler else None
+    fb = bt.fallback_steps() - fb0
+    if ws > 1:
+        dist.barrier()
+    total_ms = float(sum(tot))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    best = bt.best_lengths()
+
+    # end to end through the C ABI with host buffers: create from host
+    # coordinates, then per step iterate and read every colony's best length
+    e2e_total = 0.0
+    t0 = time.perf_counter()
+    bt2 = Batch(xys=xys, m=0, cl=w["cl"], seed=seed, device=dev, stream=stream.cuda_stream,
+                **PARAMS)
+    bt2.set_config(*tuned)
+    bt2.synchronize()
+    e2e_total += time.perf_counter() - t0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt2.iterate(1)
+        bt2.best_lengths()
+        e2e_total += time.perf_counter() - t0
+    bt2.close()
+    e2e_value = total_ants * args.steps / e2e_total
+
+    if rank == 0:
+        c_ms = statistics.mean(con)
+        draws = sum(n * (n - 1) for n in ns) * w["cl"]  # every candidate slot draws each step
+        achieved = draws / (c_ms * 1e-3)
+        peak = mmas.mmas_probe_draw_rate(dev, 50.0)
+        value = ws * total_ants * args.steps / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, **_batch_cfg(w, xys),
+                       "parallelism": f"replicas{ws}", "launch_shape": list(tuned),
+                       "l2": "flushed before every step (256 MiB write)",
+                       "timing": "CUDA events in the iteration graph, launching stream"},
+            "construct_ms": c_ms,
+            "after_construct_ms": statistics.mean(t - c for t, c in zip(tot, con)),
+            "construct_steps_per_s": sum(n * (n - 1) for n in ns) / (c_ms * 1e-3),
+            "roofline": {"kernel": "k_construct_batch", "bound": "alu", "achieved": achieved / 1e9,
+                         "peak": peak / 1e9, "unit": "Gdraws/s", "frac": achieved / peak,
+                         "peak_kind": "measured (mmas_probe_draw_rate: Philox + log2 + key per "
+                                      "draw at full occupancy, same run)",
+                         "traffic": None, "algorithmic_draws_per_launch": draws},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 4 * w["count"],
+                    "note": "create from host coordinates + per step iterate and read all best lengths"},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+            "best_len_mean": float(np.mean(best)), "fallback_steps": int(fb),
+            "wall_s": wall,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_batch(w, xys)
+        print(json.dumps(line), flush=True)
+    bt.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's iteration budget, capped)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform-n1000-cl32")
@@ -399,7 +590,11 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[args.workload]
+    if w["kind"] == "batched":
+        (run_reference_batch if args.impl == "reference" else run_ours_batch)(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_ours(args, w)

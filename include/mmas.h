@@ -211,6 +211,15 @@ mmas_status mmas_enable_phase_timing(mmas_handle *h, int32_t enable);
  * timed iteration has run. */
 mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms, float *total_ms);
 
+/* Measurement aid (not part of the method): the arithmetic ceiling of one
+ * selection on device `device`.  Runs only the per-candidate work of a
+ * candidate-list step (Alg. 4 with log keys, Sec. 4.2.2) -- one Philox4x32-10
+ * output word, its (0,1) uniform, log2, the key multiply and a running maximum
+ * -- at full occupancy for about ms milliseconds, and writes the rate in draws
+ * per second to *draws_per_s.  Synchronous; allocates and frees a small device
+ * buffer.  Errors: EINVAL (NULL output, ms <= 0), ECUDA. */
+mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s);
+
 /* ---- batched colonies -----------------------------------------------------
  *
  * Many independent colonies, on instances of uneven size, advanced together.

@@ -1,0 +1,97 @@
+// Measurement aid: the arithmetic ceiling of one selection (mmas_probe_draw_rate,
+// include/mmas.h).
+//
+// A candidate-list step costs, per candidate slot, one Philox4x32-10 output
+// word (a call yields four), the (0,1) uniform, an accurate log2, the key
+// multiply by the reciprocal weight and a running maximum of the ordered key
+// (Alg. 4 with log keys, Sec. 4.2.2).  This kernel runs exactly that work and
+// nothing else -- no table loads, no tabu, no reductions -- at full occupancy,
+// so its draw rate is the ALU ceiling the construction is measured against.
+#include <algorithm>
+#include <string>
+
+#include "internal.cuh"
+#include "mmas.h"
+
+namespace mmas {
+namespace {
+
+__global__ void __launch_bounds__(256) k_draw_probe(ConstructArgs a, int iters, uint32_t *out)
+{
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const float wi = 1.0f + (float)(threadIdx.x & 31) * 0.0625f;  // a reciprocal weight per slot
+    uint32_t best = 0;
+    for (int i = 0; i < iters; ++i) {
+        uint4 r = make_uint4(threadIdx.x & 31, (uint32_t)i, g >> 5, 0x5EEDu);
+        philox_rounds_rk<0, 10>(r, a.rk0, a.rk1);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t k = ord_key(__fmul_rn(log2f(unit_open(w[e])), wi));
+            best = k > best ? k : best;
+        }
+    }
+    out[g] = best;
+}
+
+}  // namespace
+}  // namespace mmas
+
+using namespace mmas;
+
+extern "C" mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s)
+{
+    if (!draws_per_s || !(ms > 0.0f)) {
+        set_thread_error("mmas_probe_draw_rate: draws_per_s must be non-NULL and ms > 0");
+        return MMAS_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
+    uint32_t *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double rate = 0.0;
+    if (e == cudaSuccess) {
+        // full occupancy: as many 256-thread CTAs as fit, one wave
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_draw_probe, 256, 0);
+        const int grid = prop.multiProcessorCount * (per_sm > 0 ? per_sm : 1);
+        const size_t threads = (size_t)grid * 256;
+        ConstructArgs a{};
+        for (int r = 0; r < 10; ++r) {
+            a.rk0[r] = 0x1234u + (uint32_t)r * 0x9E3779B9u;
+            a.rk1[r] = 0x5678u + (uint32_t)r * 0xBB67AE85u;
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&out, threads * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        int iters = 64;
+        float t = 0.0f;
+        // grow the launch until it runs for about `ms` (and at least 1 ms)
+        for (int tries = 0; e == cudaSuccess && tries < 16; ++tries) {
+            k_draw_probe<<<grid, 256>>>(a, iters, out);  // warm-up at this size
+            cudaEventRecord(e0);
+            k_draw_probe<<<grid, 256>>>(a, iters, out);
+            cudaEventRecord(e1);
+            e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) break;
+            rate = (double)threads * iters * 4.0 / (t * 1e-3);
+            if (t >= ms || (t >= 1.0f && iters > (1 << 26))) break;
+            const double scale = t > 0.0f ? ms / t : 64.0;
+            iters = (int)std::min<double>((double)iters * (scale < 64.0 ? scale * 1.1 : 64.0), 1 << 28);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (out) cudaFree(out);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("mmas_probe_draw_rate: ") + cudaGetErrorString(e));
+        return MMAS_ECUDA;
+    }
+    *draws_per_s = rate;
+    return MMAS_OK;
+}

@@ -28,7 +28,7 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
-           "mmas_phase_times", "mmas_score_tours_noalloc",
+           "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate",
            "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
            "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
            "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
             "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
             "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+            "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
             "mmas_batch_create": (C.c_int, [P(mmas_instance), i32, P(mmas_params), P(H)]),
             "mmas_batch_iterate": (C.c_int, [H, i32]),
             "mmas_batch_best_tour": (C.c_int, [H, i32, P(i32), P(i32)]),
@@ -355,6 +356,14 @@ class Colony:
 
     def phase_times(self):
         return mmas_phase_times(self._h)
+
+
+def mmas_probe_draw_rate(device: int = 0, ms: float = 50.0) -> float:
+    """Draws per second of the selection's per-candidate arithmetic at full
+    occupancy (a measurement aid; see include/mmas.h)."""
+    v = C.c_double()
+    _check(None, load().mmas_probe_draw_rate(device, ms, C.byref(v)))
+    return v.value
 
 
 # ------------------------------------------------------------------- batches
