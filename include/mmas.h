@@ -220,6 +220,24 @@ mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms
  * buffer.  Errors: EINVAL (NULL output, ms <= 0), ECUDA. */
 mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s);
 
+/* ---- learned edge prior: tensor-core GEMM ---------------------------------
+ *
+ * BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory),
+ * the dense contraction of the learned edge prior (a message-passing network
+ * over the candidate-list graph; not in the paper):
+ *   out[m][j] = act( sum_k A[m][k] * B[j][k] + bias[j] ),  0 <= j < n
+ *   d_a   device bf16, m rows of k values, row stride lda >= k (elements)
+ *   d_b   device bf16, n rows of k values, row stride ldb >= k
+ *   d_bias device fp32 [n] or NULL;  relu != 0 applies max(x, 0)
+ *   d_out device fp32, m rows, row stride ldd >= n
+ *   1 <= n <= 128 (tiles of 64 or 128 columns), m >= 0, k >= 0 arbitrary.
+ * Synchronises `stream` (a cudaStream_t, NULL: legacy) before returning.
+ * Errors: EINVAL (message in mmas_last_error(NULL)), ECUDA, ETIMEOUT (an MMA
+ * did not complete within 2 s). */
+mmas_status mmas_gemm_bf16(const void *d_a, int32_t lda, const void *d_b, int32_t ldb,
+                           const float *d_bias, float *d_out, int32_t ldd, int32_t m, int32_t n,
+                           int32_t k, int32_t relu, void *stream);
+
 /* ---- batched colonies -----------------------------------------------------
  *
  * Many independent colonies, on instances of uneven size, advanced together.

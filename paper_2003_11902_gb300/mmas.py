@@ -28,7 +28,7 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
-           "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate",
+           "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
            "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
            "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
            "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
             "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
             "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
+            "mmas_gemm_bf16": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, C.c_void_p,
+                                        i32, i32, i32, i32, i32, C.c_void_p]),
             "mmas_batch_create": (C.c_int, [P(mmas_instance), i32, P(mmas_params), P(H)]),
             "mmas_batch_iterate": (C.c_int, [H, i32]),
             "mmas_batch_best_tour": (C.c_int, [H, i32, P(i32), P(i32)]),
@@ -364,6 +366,16 @@ def mmas_probe_draw_rate(device: int = 0, ms: float = 50.0) -> float:
     v = C.c_double()
     _check(None, load().mmas_probe_draw_rate(device, ms, C.byref(v)))
     return v.value
+
+
+def mmas_gemm_bf16(d_a: int, lda: int, d_b: int, ldb: int, d_bias, d_out: int, ldd: int,
+                   m: int, n: int, k: int, relu: bool = False, stream=None):
+    """out = act(A B^T + bias) on the tensor cores; every pointer is a device
+    address (e.g. a torch tensor's data_ptr()); see include/mmas.h."""
+    if stream is None:
+        stream = _torch_stream()
+    _check(None, load().mmas_gemm_bf16(d_a, lda, d_b, ldb, d_bias, d_out, ldd, m, n, k,
+                                       int(relu), stream))
 
 
 # ------------------------------------------------------------------- batches

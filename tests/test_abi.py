@@ -21,12 +21,12 @@ def lib():
 def _declared():
     text = open(os.path.join(ROOT, "include", "mmas.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mmas_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mmas_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
     declared = _declared()
-    assert len(declared) == 33
+    assert len(declared) == 34
     assert sorted(mmas.EXPORTS) == declared
     for name in declared:
         assert hasattr(lib, name), name
