@@ -119,3 +119,27 @@ def random_pheromone(n: int, seed: int, lo: float, hi: float) -> np.ndarray:
     t = t + t.T
     np.fill_diagonal(t, 0.0)
     return np.ascontiguousarray(t.astype(np.float32))
+
+
+# Parameter vector of the learned edge prior (layout in include/mmas.h):
+# (name, rows, cols) for W0 [64][8], b0, W1..W3 [64][128] with biases, Wq [64][64], a, c.
+PRIOR_LAYOUT = [("W0", 64, 8), ("b0", 64, 1), ("W1", 64, 128), ("b1", 64, 1), ("W2", 64, 128),
+                ("b2", 64, 1), ("W3", 64, 128), ("b3", 64, 1), ("Wq", 64, 64), ("a", 1, 1),
+                ("c", 1, 1)]
+
+
+def prior_params(seed: int) -> np.ndarray:
+    """Seeded initial parameters of the learned prior, float32: weight matrices
+    N(0, 1/cols), the layer weights halved (the residual stack stays stable),
+    zero biases, a = -1, c = 0."""
+    rng = _rng(seed)
+    parts = []
+    for name, rows, cols in PRIOR_LAYOUT:
+        if name.startswith("W"):
+            std = (1.0 / cols) ** 0.5 * (0.5 if name in ("W1", "W2", "W3") else 1.0)
+            parts.append(rng.standard_normal(rows * cols) * std)
+        elif name == "a":
+            parts.append(np.array([-1.0]))
+        else:
+            parts.append(np.zeros(rows * cols))
+    return np.concatenate(parts).astype(np.float32)
