@@ -238,6 +238,52 @@ mmas_status mmas_gemm_bf16(const void *d_a, int32_t lda, const void *d_b, int32_
                            const float *d_bias, float *d_out, int32_t ldd, int32_t m, int32_t n,
                            int32_t k, int32_t relu, void *stream);
 
+/* ---- learned edge prior ---------------------------------------------------
+ *
+ * A 3-layer message-passing network over each node's 16 nearest neighbours
+ * (the first 16 entries of a colony's candidate lists, so cl >= 16; the
+ * instance must have coordinates) scores every candidate edge; its edge
+ * probabilities sigmoid(s) replace eta^beta in that colony's choice_info (an
+ * extension of this library; plain MMAS with eta = 1/d stays available and is
+ * the reference).  Hidden width 64; every dense product runs on the tensor
+ * cores (bf16 operands, fp32 accumulation).
+ *   features  F0[i] = ((x-cx)/s, (y-cy)/s, d(i,nn0)/D, d(i,nn1)/D, d(i,nn3)/D,
+ *             d(i,nn15)/D, 1, 0): (cx, cy) the centre of the coordinates'
+ *             bounding box, s its longer side, D = max_i d(i, nn[i][15])
+ *   h0 = relu(F0 W0^T + b0);  for l = 1..3: m_i = mean_k h[nn[i][k]],
+ *   h = relu([h | m] W_l^T + b_l) + h;  q = h Wq^T;
+ *   s[i][k] = <q_i, h[nn[i][k]]> / 8 + a d(i,nn[i][k])/D + c
+ * Parameters, fp32, in this order: W0 [64][8], b0 [64], W1 [64][128], b1 [64],
+ * W2, b2, W3, b3, Wq [64][64], a, c  (MMAS_PRIOR_PARAMS values; weights
+ * row-major [out][in]).  Every call enqueues on the colony's stream and
+ * synchronises it before returning.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+typedef struct mmas_prior mmas_prior;
+#define MMAS_PRIOR_PARAMS 29442
+
+/* params: host, MMAS_PRIOR_PARAMS floats, or NULL for zeros. */
+mmas_status mmas_prior_create(const float *params, int32_t device, mmas_prior **out);
+/* Replace the parameters (and reset the optimiser state). */
+mmas_status mmas_prior_set_params(mmas_prior *p, const float *params);
+mmas_status mmas_prior_get_params(mmas_prior *p, float *params);
+/* Scores s [n][16] (host, row-major) of colony h's candidate edges. */
+mmas_status mmas_prior_scores(mmas_prior *p, mmas_handle *h, float *scores);
+/* `steps` Adam steps (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the mean binary
+ * cross-entropy of sigmoid(s) against y[i][k] = [(i, nn[i][k]) is an edge of
+ * `tour`] (host, a permutation of 0..n-1); *loss (may be NULL) = the loss of
+ * the last step's forward pass. */
+mmas_status mmas_prior_train(mmas_prior *p, mmas_handle *h, const int32_t *tour, int32_t steps, float lr,
+                             float *loss);
+/* The gradient of that loss at the current parameters (host, MMAS_PRIOR_PARAMS
+ * floats) without changing the parameters or the optimiser state. */
+mmas_status mmas_prior_grad(mmas_prior *p, mmas_handle *h, const int32_t *tour, float *grad, float *loss);
+/* Replace colony h's eta^beta: the 16 candidates of row i take sigmoid(s[i][k]);
+ * every other entry keeps d^-beta scaled by min_k sigmoid(s[i][k]) / (the 16th
+ * candidate's d^-beta).  Then choice_info is refreshed from the current
+ * pheromone.  The colony's pheromone, limits and iteration index are unchanged. */
+mmas_status mmas_prior_apply(mmas_prior *p, mmas_handle *h);
+void mmas_prior_destroy(mmas_prior *p);
+const char *mmas_prior_last_error(const mmas_prior *p);
+
 /* ---- batched colonies -----------------------------------------------------
  *
  * Many independent colonies, on instances of uneven size, advanced together.

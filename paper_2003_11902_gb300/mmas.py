@@ -29,6 +29,9 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
+           "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
+           "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
+           "mmas_prior_destroy", "mmas_prior_last_error",
            "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
            "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
            "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
@@ -105,6 +108,15 @@ def load(path: str = LIB_PATH):
             "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
             "mmas_gemm_bf16": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, C.c_void_p,
                                         i32, i32, i32, i32, i32, C.c_void_p]),
+            "mmas_prior_create": (C.c_int, [P(f32), i32, P(H)]),
+            "mmas_prior_set_params": (C.c_int, [H, P(f32)]),
+            "mmas_prior_get_params": (C.c_int, [H, P(f32)]),
+            "mmas_prior_scores": (C.c_int, [H, H, P(f32)]),
+            "mmas_prior_train": (C.c_int, [H, H, P(i32), i32, f32, P(f32)]),
+            "mmas_prior_grad": (C.c_int, [H, H, P(i32), P(f32), P(f32)]),
+            "mmas_prior_apply": (C.c_int, [H, H]),
+            "mmas_prior_destroy": (None, [H]),
+            "mmas_prior_last_error": (C.c_char_p, [H]),
             "mmas_batch_create": (C.c_int, [P(mmas_instance), i32, P(mmas_params), P(H)]),
             "mmas_batch_iterate": (C.c_int, [H, i32]),
             "mmas_batch_best_tour": (C.c_int, [H, i32, P(i32), P(i32)]),
@@ -376,6 +388,68 @@ def mmas_gemm_bf16(d_a: int, lda: int, d_b: int, ldb: int, d_bias, d_out: int, l
         stream = _torch_stream()
     _check(None, load().mmas_gemm_bf16(d_a, lda, d_b, ldb, d_bias, d_out, ldd, m, n, k,
                                        int(relu), stream))
+
+
+# ------------------------------------------------------------------- learned prior
+
+MMAS_PRIOR_PARAMS = 29442
+
+
+def _pcheck(p, status):
+    if status != MMAS_OK:
+        msg = load().mmas_prior_last_error(p)
+        raise MMASError(status, msg.decode() if msg else "")
+
+
+class Prior:
+    """The learned edge prior (see include/mmas.h): a message-passing network
+    whose edge probabilities can replace a colony's eta^beta."""
+
+    def __init__(self, params=None, device=0):
+        h = C.c_void_p()
+        if params is not None:
+            params = np.ascontiguousarray(params, dtype=np.float32)
+            assert params.size == MMAS_PRIOR_PARAMS
+        _pcheck(None, load().mmas_prior_create(_f32p(params) if params is not None else None, device,
+                                               C.byref(h)))
+        self._p = h
+
+    def close(self):
+        if getattr(self, "_p", None):
+            load().mmas_prior_destroy(self._p)
+            self._p = None
+
+    __del__ = close
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        _pcheck(self._p, load().mmas_prior_set_params(self._p, _f32p(params)))
+
+    def params(self):
+        out = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
+        _pcheck(self._p, load().mmas_prior_get_params(self._p, _f32p(out)))
+        return out
+
+    def scores(self, colony: "Colony"):
+        out = np.zeros((colony.n, 16), np.float32)
+        _pcheck(self._p, load().mmas_prior_scores(self._p, colony._h, _f32p(out)))
+        return out
+
+    def train(self, colony: "Colony", tour, steps: int = 1, lr: float = 1e-3) -> float:
+        t = np.ascontiguousarray(tour, dtype=np.int32)
+        loss = C.c_float()
+        _pcheck(self._p, load().mmas_prior_train(self._p, colony._h, _i32p(t), steps, lr, C.byref(loss)))
+        return loss.value
+
+    def grad(self, colony: "Colony", tour):
+        t = np.ascontiguousarray(tour, dtype=np.int32)
+        g = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
+        loss = C.c_float()
+        _pcheck(self._p, load().mmas_prior_grad(self._p, colony._h, _i32p(t), _f32p(g), C.byref(loss)))
+        return g, loss.value
+
+    def apply(self, colony: "Colony"):
+        _pcheck(self._p, load().mmas_prior_apply(self._p, colony._h))
 
 
 # ------------------------------------------------------------------- batches
