@@ -50,9 +50,16 @@ WORKLOADS = {
     # seed 1000 + i, m = n each
     "batched-256-n100-2000-cl32": dict(kind="batched", count=256, lo=100, hi=2000, cl=32,
                                        size_seed=1000),
+    # the learned edge prior: trained on elite tours of generated instances (n log-uniform in
+    # [200, 2000], coordinate seeds 5000 + i), then plain and prior MMAS raced on the n = 1000
+    # instance (cl = 16, 2-opt of the iteration best) for equal wall time
+    "learned-prior-n1000-cl16-2opt": dict(kind="prior", n=1000, m=1000, cl=16, iseed=1001, ls=1,
+                                          train_count=16, train_seed=2000, train_iters=40,
+                                          train_steps=40, lr=2e-3, race_s=1.5),
 }
 DEFAULT_STEPS = {"uniform-n1000-cl32": 1000, "uniform-n200-fullrow": 1000,
-                 "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30}
+                 "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30,
+                 "learned-prior-n1000-cl16-2opt": 200}
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
 # kernels in one iteration graph: construct, score, update; with 2-opt of the
 # iteration best also the 2-opt and the best/limits kernel; with 2-opt of every
@@ -67,7 +74,7 @@ CONSTRUCT_SOURCES = ["paper_2003_11902_gb300/csrc/construct.cu",
 
 def _instance(w):
     from paper_2003_11902_gb300 import instances as I
-    if w["kind"] == "uniform":
+    if w["kind"] in ("uniform", "prior"):
         return I.uniform(w["n"], w["iseed"])
     return I.clustered(w["n"], w["iseed"])
 
@@ -576,6 +583,136 @@ def run_ours_batch(args, w):
         dist.destroy_process_group()
 
 
+def _race(col, seconds, target, check_every=5):
+    """Iterate until `seconds` of wall time; the best length after each check
+    and the time at which it first reached `target`."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trace, hit = [], None
+    while True:
+        col.iterate(check_every)
+        best = col.stats()["best_len"]
+        el = time.perf_counter() - t0
+        trace.append((round(el, 4), int(best)))
+        if hit is None and best <= target:
+            hit = el
+        if el >= seconds:
+            break
+    return trace, hit
+
+
+def run_ours_prior(args, w):
+    import torch
+
+    from paper_2003_11902_gb300 import Colony, Prior, _build
+    from paper_2003_11902_gb300 import instances as I
+
+    _, rank, _ = _dist_env()
+    dev = torch.cuda.current_device()
+    _build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    common = dict(cl=w["cl"], device=dev, ls=w["ls"], stream=stream.cuda_stream, **PARAMS)
+    # ---- training on elite tours of generated instances
+    prior = Prior(I.prior_params(1), device=dev)
+    sizes = I.log_uniform_sizes(w["train_count"], w["train_seed"], 200, 2000)
+    t0 = time.perf_counter()
+    losses = []
+    for i, n in enumerate(sizes):
+        col = Colony(xy=I.uniform(int(n), 5000 + i), m=int(n), seed=100 + i, **common)
+        col.iterate(w["train_iters"])
+        _, elite = col.best_tour()
+        first = prior.train(col, elite, steps=1, lr=w["lr"])
+        last = prior.train(col, elite, steps=w["train_steps"] - 1, lr=w["lr"])
+        losses.append((round(first, 4), round(last, 4)))
+        col.close()
+    train_s = time.perf_counter() - t0
+    # ---- equal-wall-time race on the evaluation instance
+    xy = _instance(w)
+    path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
+    with open(path) as f:
+        lstar = json.load(f)["lstar"]
+    target = 1.02 * lstar
+    plain = Colony(xy=xy, m=w["m"], seed=1, **common)
+    guided = Colony(xy=xy, m=w["m"], seed=1, **common)
+    t0 = time.perf_counter()
+    prior.apply(guided)
+    apply_s = time.perf_counter() - t0
+    plain.iterate(2)
+    guided.iterate(2)
+    race = {}
+    for name, col in (("plain", plain), ("prior", guided)):
+        trace, hit = _race(col, w["race_s"], target)
+        race[name] = {"best_at_end": trace[-1][1], "seconds_to_2pct": hit, "trace": trace[::4]}
+    plain.close()
+    # ---- throughput of the prior-guided colony (as for the other workloads)
+    guided.enable_phase_timing(True)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        guided.iterate(1)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev) if rank == 0 else None
+    con, tot = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        guided.iterate(1)
+        c, _, t = guided.phase_times()
+        con.append(c)
+        tot.append(t)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    total_ms = float(sum(tot))
+    # end to end: create from host coordinates, apply the prior, then per step
+    # iterate and read the best tour back
+    t0 = time.perf_counter()
+    e2e_col = Colony(xy=xy, m=w["m"], seed=1, **common)
+    prior.apply(e2e_col)
+    for _ in range(args.steps):
+        e2e_col.iterate(1)
+        e2e_col.best_tour()
+    e2e_s = time.perf_counter() - t0
+    e2e_col.close()
+    guided.close()
+    prior.close()
+    peak, peak_kind = _peaks()
+    c_ms = statistics.mean(con)
+    wc = dict(w, n=w["n"], m=w["m"], cl=w["cl"])
+    algo = algorithmic_construct_bytes(wc)
+    line = {
+        "metric": METRIC, "value": w["m"] * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": w["n"], "m": w["m"], "cl": w["cl"],
+                   "instance": f"uniform seed {w['iseed']}", "local_search": "2-opt of the iteration best",
+                   "heuristic": "learned edge prior (3-layer message passing, hidden 64, bf16 tensor cores)",
+                   **PARAMS, "parallelism": "replicas1",
+                   "l2": "flushed before every step (256 MiB write)",
+                   "timing": "CUDA events in the iteration graph, launching stream"},
+        "construct_ms": c_ms,
+        "after_construct_ms": statistics.mean(t - c for t, c in zip(tot, con)),
+        "roofline": {"kernel": "k_construct", "bound": "hbm", "achieved": algo / (c_ms * 1e-3) / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": algo / (c_ms * 1e-3) / 1e9 / peak,
+                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": algo},
+        "e2e": {"value": w["m"] * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 * w["n"] + 64,
+                "note": "create + apply the trained prior + per step iterate and read the best tour"},
+        "gpu_launches": KERNELS_PER_ITERATION[w["ls"]] * args.steps,
+        "clocks": clocks,
+        "learned_prior": {
+            "train_instances": len(sizes), "train_sizes": [int(x) for x in sizes],
+            "train_s": round(train_s, 3), "loss_first_last": losses, "apply_s": round(apply_s, 4),
+            "race_seconds": w["race_s"], "target": target, "lstar": lstar,
+            "lstar_source": "tests/golden/lstar_uniform_n1000.json (oracle, cl = 32, no local search)",
+            "race": race},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(dict(w, m=w["m"]), xy)
+        line["cpu_baseline"]["sample"] += " (plain MMAS: the oracle has no learned prior)"
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -594,6 +731,8 @@ def main():
         args.steps = DEFAULT_STEPS[args.workload]
     if w["kind"] == "batched":
         (run_reference_batch if args.impl == "reference" else run_ours_batch)(args, w)
+    elif w["kind"] == "prior" and args.impl != "reference":
+        run_ours_prior(args, w)
     elif args.impl == "reference":
         run_reference(args, w)
     else:
