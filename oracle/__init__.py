@@ -65,6 +65,10 @@ def lib():
                 "orc_word_start": (u32, [u64, i32, i32]),
                 "orc_word_cand": (u32, [u64, i32, i32, i32, i32]),
                 "orc_word_row": (u32, [u64, i32, i32, i32, i32]),
+                "orc_word_slot": (u32, [u64, i32, i32, i32, i32]),
+                "orc_word_rwm": (u32, [u64, i32, i32, i32]),
+                "orc_rwm_rounds": (i32, [i32, P(f32), f32]),
+                "orc_colony_set_variant": (None, [vp, i32, i32]),
                 "orc_start_node": (i32, [u64, i32, i32, i32]),
                 "orc_isqrt64": (u64, [u64]),
                 "orc_euc2d": (i64, [i32, i32, i32, i32]),
@@ -226,6 +230,21 @@ def rwm_pick(w, u) -> int:
     return lib().orc_rwm_pick(len(w), _f64p(w), float(u))
 
 
+def rwm_rounds(x, u) -> int:
+    """The exact single-precision parallel roulette wheel over weights x (see
+    orc_rwm_rounds); returns the winning position or -1."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return lib().orc_rwm_rounds(x.size, _f32p(x), float(np.float32(u)))
+
+
+def word_slot(seed, it, ant, t, j):
+    return lib().orc_word_slot(seed, it, ant, t, j)
+
+
+def word_rwm(seed, it, ant, t):
+    return lib().orc_word_rwm(seed, it, ant, t)
+
+
 def two_opt(d, nn, tour):
     """2-opt with neighbour lists nn (n x k) and don't-look bits; returns
     (improved tour, number of moves)."""
@@ -250,7 +269,7 @@ class Colony:
     """The oracle's MMAS (Alg. 1) on one instance; same parameters as the C ABI."""
 
     def __init__(self, n=None, xy=None, dist=None, m=1, cl=0, alpha=1.0, beta=2.0, rho=0.02,
-                 p_best=0.01, seed=1, deposit=0, fallback=0, ls=0):
+                 p_best=0.01, seed=1, deposit=0, fallback=0, ls=0, selection=0, tabu=0):
         if (xy is None) == (dist is None):
             raise ValueError("give exactly one of xy and dist")
         if xy is not None:
@@ -266,9 +285,13 @@ class Colony:
         if ls and cl < 1:
             raise ValueError("local search uses the candidate lists: cl must be >= 1")
         self.ls = ls
+        if (selection or tabu) and cl != 0:
+            raise ValueError("the roulette wheel and the compact tabu are whole-row variants (cl = 0)")
+        self.selection, self.tabu = selection, tabu
         self._h = lib().orc_colony_new(n, xyp, dp, m, cl, float(alpha), float(beta),
                                        float(np.float32(rho)), float(p_best), int(seed),
                                        deposit, fallback, ls)
+        lib().orc_colony_set_variant(self._h, int(selection), int(tabu))
 
     def __del__(self):
         h = getattr(self, "_h", None)

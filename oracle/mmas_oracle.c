@@ -120,6 +120,24 @@ ORC_API uint32_t orc_word_row(uint64_t seed, int32_t it, int32_t ant, int32_t t,
     return o[v & 3];
 }
 
+/* Whole-row variants (Sec. 4.1 compact tabu, Sec. 4.2.1 roulette wheel):
+ * the reservoir draw of slot j of the compact list at step t, and the single
+ * roulette-wheel draw of step t. */
+ORC_API uint32_t orc_word_slot(uint64_t seed, int32_t it, int32_t ant, int32_t t, int32_t j)
+{
+    uint32_t o[4];
+    philox_seeded(seed, 0x40000000u | ((uint32_t)j >> 2), (uint32_t)t, (uint32_t)ant,
+                  (uint32_t)it, o);
+    return o[j & 3];
+}
+
+ORC_API uint32_t orc_word_rwm(uint64_t seed, int32_t it, int32_t ant, int32_t t)
+{
+    uint32_t o[4];
+    philox_seeded(seed, 0xFFFFFFFEu, (uint32_t)t, (uint32_t)ant, (uint32_t)it, o);
+    return o[0];
+}
+
 /* floor(x * n / 2^32): the start node for a 32-bit word x. */
 ORC_API int32_t orc_start_node(uint64_t seed, int32_t it, int32_t ant, int32_t n)
 {
@@ -327,6 +345,65 @@ ORC_API int32_t orc_rwm_pick(int32_t k, const double *w, double u)
     return k - 1;
 }
 
+/* The parallel roulette wheel (Sec. 4.2.1) as one exact single-precision
+ * procedure, so that a 32-lane GPU implementation and this sequential one
+ * pick the same position.  Weights x[0..N) (0 = not selectable) are taken in
+ * rounds of 128 positions; in round r, lane l (0..31) owns positions
+ * 128r + 4l .. 128r + 4l + 3 and forms its running partial sums
+ * q0 = x0, q1 = q0 + x1, q2 = q1 + x2, q3 = q2 + x3; the lanes' totals q3 are
+ * scanned inclusively (Hillis-Steele: for d = 1, 2, 4, 8, 16, S_l <- S_l +
+ * S_{l-d} when l >= d); the rounds' totals S_31 accumulate into an offset O.
+ * With the total T (the final O) and theta = u * T, the winner is the first
+ * position p with x_p > 0 whose cumulative sum (O_r + S_{l-1}) + q_e exceeds
+ * theta (S_{-1} = 0); if rounding leaves none, the last position with
+ * x_p > 0.  Every operation is a float add or multiply rounded to nearest.
+ * Returns -1 when no weight is positive. */
+static void rwm_round(const float *x, int32_t N, int32_t r, float q[32][4], float S[32])
+{
+    for (int l = 0; l < 32; ++l) {
+        float acc = 0.0f;
+        for (int e = 0; e < 4; ++e) {
+            const int32_t p = 128 * r + 4 * l + e;
+            const float v = p < N ? x[p] : 0.0f;
+            acc = e == 0 ? v : acc + v;
+            q[l][e] = acc;
+        }
+        S[l] = acc;
+    }
+    for (int d = 1; d < 32; d <<= 1) {
+        float T[32];
+        for (int l = 0; l < 32; ++l) T[l] = l >= d ? S[l] + S[l - d] : S[l];
+        memcpy(S, T, sizeof(T));
+    }
+}
+
+ORC_API int32_t orc_rwm_rounds(int32_t N, const float *x, float u)
+{
+    const int32_t rounds = (N + 127) / 128;
+    float q[32][4], S[32];
+    float total = 0.0f;
+    for (int32_t r = 0; r < rounds; ++r) {
+        rwm_round(x, N, r, q, S);
+        total = total + S[31];
+    }
+    const float theta = u * total;
+    float off = 0.0f;
+    for (int32_t r = 0; r < rounds; ++r) {
+        rwm_round(x, N, r, q, S);
+        for (int l = 0; l < 32; ++l) {
+            const float base = off + (l > 0 ? S[l - 1] : 0.0f);
+            for (int e = 0; e < 4; ++e) {
+                const int32_t p = 128 * r + 4 * l + e;
+                if (p < N && x[p] > 0.0f && base + q[l][e] > theta) return p;
+            }
+        }
+        off = off + S[31];
+    }
+    for (int32_t p = N - 1; p >= 0; --p)
+        if (x[p] > 0.0f) return p;
+    return -1;
+}
+
 ORC_API int64_t orc_two_opt(int32_t n, const int32_t *d, const int32_t *nn, int32_t k,
                             int32_t *tour);
 
@@ -336,6 +413,8 @@ ORC_API int64_t orc_two_opt(int32_t n, const int32_t *d, const int32_t *nn, int3
 
 typedef struct orc_colony {
     int32_t n, m, cl, deposit, fallback, ls;
+    int32_t sel;       /* whole-row selection: 0 reservoir sampling, 1 roulette wheel */
+    int32_t tabu;      /* whole-row tabu: 0 bitmask, 1 compact list (Sec. 4.1) */
     double alpha, beta, rho, p_best;
     float persist;
     uint64_t seed;
@@ -366,6 +445,7 @@ ORC_API orc_colony *orc_colony_new(int32_t n, const int32_t *xy, const int32_t *
     orc_colony *c = (orc_colony *)calloc(1, sizeof(orc_colony));
     size_t nn = (size_t)n * n;
     c->n = n; c->m = m; c->cl = cl; c->deposit = deposit; c->fallback = fallback; c->ls = ls;
+    c->sel = 0; c->tabu = 0;
     c->alpha = alpha; c->beta = beta; c->rho = (double)rho; c->p_best = p_best;
     c->persist = (float)(1.0 - (double)rho);
     c->seed = seed;
@@ -451,12 +531,101 @@ static int32_t argmax_keys(int32_t n, const double *keys)
     return best;
 }
 
+/* Whole-row variants (cl = 0 only): selection 0 = reservoir sampling, 1 =
+ * roulette wheel; tabu 0 = bitmask, 1 = compact list. */
+ORC_API void orc_colony_set_variant(orc_colony *c, int32_t sel, int32_t tabu)
+{
+    c->sel = sel;
+    c->tabu = tabu;
+}
+
+/* A whole-row tour under the selected variant.  The compact list (Sec. 4.1):
+ * entries[0..L) are the unvisited nodes; removing the node at slot j moves
+ * the last one, t = entries[L-1], into slot j and records entries[t] = j
+ * (when j < L-1), or marks entries[j] = n (when j = L-1); then L decreases.
+ * Reservoir sampling over the list draws slot j's uniform from
+ * orc_word_slot and keeps the largest log2(r)/w (ties -> lower node id);
+ * over the bitmask it is the plain whole-row step.  The roulette wheel takes
+ * the weights in list order (compact) or node order with visited nodes at
+ * weight 0 (bitmask) and applies orc_rwm_rounds to the step's draw. */
+static int64_t construct_row_variant(const orc_colony *c, int32_t it, int32_t ant, int32_t *tour)
+{
+    const int32_t n = c->n;
+    uint8_t *vis = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *entries = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    float *x = (float *)malloc(sizeof(float) * (size_t)n);
+    double *keys = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int32_t v = 0; v < n; ++v) entries[v] = v;
+    int32_t L = n;
+    int32_t cur = orc_start_node(c->seed, it, ant, n);
+    tour[0] = cur;
+    vis[cur] = 1;
+    int32_t slot = cur;  /* the start node is at home */
+    for (int32_t t = 0; t < n; ++t) {
+        if (c->tabu) {
+            /* remove `cur` from its slot */
+            if (slot == L - 1) {
+                entries[slot] = n;
+            } else {
+                const int32_t last = entries[L - 1];
+                entries[slot] = last;
+                entries[last] = slot;
+            }
+            --L;
+        }
+        if (t == n - 1) break;
+        const float *row = c->choice + (size_t)cur * n;
+        int32_t next = -1, nslot = -1;
+        if (c->sel == 0) {
+            if (c->tabu) {
+                double bk = 0.0;
+                for (int32_t j = 0; j < L; ++j) {
+                    const int32_t v = entries[j];
+                    const double r = orc_uniform01(orc_word_slot(c->seed, it, ant, t + 1, j));
+                    const double k = log2(r) / (double)row[v];
+                    if (next < 0 || k > bk || (k == bk && v < next)) {
+                        bk = k;
+                        next = v;
+                        nslot = j;
+                    }
+                }
+            } else {
+                orc_step_keys(c, it, ant, t + 1, cur, vis, keys);
+                next = argmax_keys(n, keys);
+            }
+        } else {
+            const float u = (float)orc_uniform01(orc_word_rwm(c->seed, it, ant, t + 1));
+            if (c->tabu) {
+                for (int32_t j = 0; j < L; ++j) x[j] = row[entries[j]];
+                nslot = orc_rwm_rounds(L, x, u);
+                next = entries[nslot];
+            } else {
+                for (int32_t v = 0; v < n; ++v) x[v] = vis[v] ? 0.0f : row[v];
+                next = orc_rwm_rounds(n, x, u);
+            }
+        }
+        tour[t + 1] = next;
+        vis[next] = 1;
+        cur = next;
+        slot = nslot;
+    }
+    free(keys);
+    free(x);
+    free(entries);
+    free(vis);
+    return orc_tour_length(n, c->d, tour);
+}
+
 /* One ant's tour in iteration `it` (Alg. 1, inner loops): a random start, then
  * n-1 selections.  Returns the tour length; *fallbacks counts greedy or
  * full-row fallback steps taken after an exhausted candidate list. */
 ORC_API int64_t orc_colony_construct(const orc_colony *c, int32_t it, int32_t ant, int32_t *tour,
                                      int64_t *fallbacks)
 {
+    if (c->cl == 0 && (c->sel != 0 || c->tabu != 0)) {
+        if (fallbacks) *fallbacks = 0;
+        return construct_row_variant(c, it, ant, tour);
+    }
     int32_t n = c->n;
     uint8_t *vis = (uint8_t *)calloc((size_t)n, 1);
     double *keys = (double *)malloc(sizeof(double) * (size_t)n);

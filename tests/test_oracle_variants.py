@@ -1,0 +1,88 @@
+"""Pins of the whole-row variants of the oracle (Sec. 4.1 compact tabu, Sec.
+4.2.1 roulette wheel) by exact arithmetic and by Eq. (1)'s probabilities."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2003_11902_gb300 import instances as I
+
+scipy_stats = pytest.importorskip("scipy.stats")
+
+
+def test_roulette_pick_is_exact_up_to_float_rounding():
+    rng = np.random.default_rng(0)
+    for trial in range(300):
+        N = int(rng.integers(1, 700))
+        x = rng.uniform(0, 1, N).astype(np.float32)
+        x[rng.random(N) < 0.3] = 0.0
+        if not (x > 0).any():
+            x[int(rng.integers(0, N))] = 1.0
+        u = np.float32((int(rng.integers(0, 1 << 23)) + 0.5) / (1 << 23))
+        p = O.rwm_rounds(x, u)
+        assert p >= 0 and x[p] > 0
+        # exact cumulative sums: C(p-1) <= u T < C(p), up to 1e-5 relative (float sums)
+        fx = [Fraction(float(v)) for v in x]
+        T = sum(fx)
+        below = sum(fx[:p])
+        theta = Fraction(float(u)) * T
+        tol = T * Fraction(1, 100000)
+        assert below - tol <= theta <= below + fx[p] + tol
+
+
+def test_roulette_frequencies_follow_the_weights():
+    rng = np.random.default_rng(1)
+    x = np.zeros(300, np.float32)
+    x[rng.choice(300, 20, replace=False)] = rng.uniform(0.5, 2.0, 20)
+    counts = np.zeros(300)
+    for k in range(40000):
+        u = np.float32((O.word_rwm(7, k, 0, 1) >> 9) * 2.0 ** -23 + 2.0 ** -24)
+        counts[O.rwm_rounds(x, u)] += 1
+    sel = x > 0
+    assert counts[~sel].sum() == 0
+    xs = x[sel].astype(np.float64)
+    exp = counts.sum() * xs / xs.sum()
+    assert scipy_stats.chisquare(counts[sel], exp).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("selection,tabu", [(0, 1), (1, 0), (1, 1)])
+def test_variant_first_steps_follow_eq1(selection, tabu):
+    """From a fixed start, the second node's frequencies over many iterations
+    (draws change with the iteration index) equal p_ij of Eq. (1)."""
+    n = 12
+    xy = I.uniform(n, 5)
+    col = O.Colony(xy=xy, m=1, cl=0, rho=0.3, seed=3, selection=selection, tabu=tabu)
+    w = col.state()["choice"]
+    counts = {}
+    starts = {}
+    for it in range(6000):
+        _, tour, _ = col.construct(it, 0)
+        starts.setdefault(int(tour[0]), []).append(int(tour[1]))
+    s0 = max(starts, key=lambda k: len(starts[k]))
+    picks = np.bincount(starts[s0], minlength=n).astype(float)
+    p = w[s0].astype(np.float64).copy()
+    p[s0] = 0
+    p /= p.sum()
+    keep = p > 0
+    assert picks[~keep].sum() == 0
+    assert scipy_stats.chisquare(picks[keep], picks.sum() * p[keep]).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("selection,tabu", [(0, 1), (1, 0), (1, 1)])
+def test_variant_tours_are_permutations_and_runs_improve(selection, tabu):
+    n = 40
+    col = O.Colony(xy=I.uniform(n, 9), m=20, cl=0, rho=0.1, seed=4, selection=selection, tabu=tabu)
+    first = None
+    for it in range(15):
+        col.iterate(1)
+        tours, lens, _ = col.tours()
+        assert all(sorted(t) == list(range(n)) for t in tours)
+        if first is None:
+            first = col.best()[0]
+    assert col.best()[0] <= first
+
+
+def test_variants_need_whole_rows():
+    with pytest.raises(ValueError, match="whole-row"):
+        O.Colony(xy=I.uniform(20, 1), m=2, cl=8, selection=1)
