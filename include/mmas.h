@@ -85,6 +85,12 @@ typedef struct {
  *            improvement, cities visited in index order, runs repeated until
  *            one makes no move.  Needs cl >= 1 and 13n bytes of shared memory
  *            per CTA (n <= 17,800 on GB300)                          (0)
+ *   selection  whole-row mode (cl = 0) only: 0 weighted reservoir sampling
+ *            (Alg. 4); 1 the parallel roulette wheel (Sec. 4.2.1), one draw
+ *            per step, the exact single-precision procedure described below (0)
+ *   tabu     whole-row mode only: 0 the bitmask tabu; 1 the compact list of
+ *            unvisited nodes (Sec. 4.1): removing the node at slot j moves the
+ *            list's last node into slot j                           (0)
  *   stream   cudaStream_t to enqueue on, or NULL for a private non-blocking
  *            stream; pass cudaStreamLegacy to use the legacy default stream (NULL)
  *
@@ -92,7 +98,19 @@ typedef struct {
  * Philox(ctr = (0xFFFFFFFF, 0, k, it)); candidate slot s at step t = word
  * (t mod 4) of Philox(ctr = (s, t/4, k, it)); whole-row node v at step t =
  * word (v mod 4) of Philox(ctr = (2^31 | v/4, t, k, it)); key = (seed_lo,
- * seed_hi).  A word x maps to r = ((x >> 9) + 1/2) 2^-23 in (0,1). */
+ * seed_hi).  A word x maps to r = ((x >> 9) + 1/2) 2^-23 in (0,1).
+ * Compact-list reservoir draws: slot j at step t = word (j mod 4) of
+ * Philox(ctr = (2^30 | j/4, t, k, it)).  Roulette wheel: one draw per step,
+ * word 0 of Philox(ctr = (0xFFFFFFFE, t, k, it)), u = r in single precision.
+ * The roulette wheel takes the unvisited weights (choice_info) in node order
+ * (bitmask tabu, visited nodes at weight 0) or list order (compact tabu), in
+ * rounds of 128 positions: lane l of 32 owns positions 128r + 4l .. +3 and
+ * forms partial sums q0 = x0, q1 = q0 + x1, q2 = q1 + x2, q3 = q2 + x3; the
+ * lanes' q3 are scanned (for d = 1, 2, 4, 8, 16: S_l += S_{l-d} when l >= d)
+ * and the rounds' totals S_31 accumulate into the offset O; with T = the
+ * final O and theta = u T, the pick is the first position p with x_p > 0 and
+ * (O_r + S_{l-1}) + q_e > theta (S_{-1} = 0), else the last p with x_p > 0;
+ * every operation is a float add or multiply rounded to nearest. */
 typedef struct {
     int32_t m;
     float alpha;
@@ -106,6 +124,8 @@ typedef struct {
     int32_t device;
     int32_t ant_offset;
     int32_t ls;
+    int32_t selection;
+    int32_t tabu;
     void *stream;
 } mmas_params;
 

@@ -521,6 +521,226 @@ __global__ void __launch_bounds__(384, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Whole-row variants (Sec. 4.1 compact tabu, Sec. 4.2.1 roulette wheel).
+// ---------------------------------------------------------------------------
+
+// Running partial sums q[0..3] of lane l's four positions 128r + 4l .. +3 of
+// round r, x() giving each position's weight (0 beyond N), plus the weights.
+template <class X>
+__device__ __forceinline__ void rwm_lane(X x, int r, int lane, int N, float (&w)[4], float (&q)[4])
+{
+    const int p0 = 128 * r + 4 * lane;
+    x(p0, N, w);
+    q[0] = w[0];
+    q[1] = __fadd_rn(q[0], w[1]);
+    q[2] = __fadd_rn(q[1], w[2]);
+    q[3] = __fadd_rn(q[2], w[3]);
+}
+
+// Inclusive lane scan, S_l <- S_l + S_{l-d} for d = 1, 2, 4, 8, 16.
+__device__ __forceinline__ float rwm_scan(float S, int lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float v = __shfl_up_sync(FULL, S, d);
+        if (lane >= d) S = __fadd_rn(S, v);
+    }
+    return S;
+}
+
+// The parallel roulette wheel over positions [0, N) with draw u: the exact
+// single-precision procedure (rounds of 128 positions, lane partial sums,
+// lane scan, running round offset; first position whose cumulative sum
+// exceeds u * total, else the last positive one).  Every lane returns it;
+// -1 when no weight is positive.
+template <class X>
+__device__ __forceinline__ int rwm_pick(X x, int N, float u, int lane)
+{
+    const int rounds = (N + 127) >> 7;
+    float total = 0.0f;
+    for (int r = 0; r < rounds; ++r) {
+        float w[4], q[4];
+        rwm_lane(x, r, lane, N, w, q);
+        total = __fadd_rn(total, __shfl_sync(FULL, rwm_scan(q[3], lane), 31));
+    }
+    const float theta = __fmul_rn(u, total);
+    float off = 0.0f;
+    int last = -1;
+    for (int r = 0; r < rounds; ++r) {
+        float w[4], q[4];
+        rwm_lane(x, r, lane, N, w, q);
+        const float S = rwm_scan(q[3], lane);
+        float prev = __shfl_up_sync(FULL, S, 1);
+        if (lane == 0) prev = 0.0f;
+        const float base = __fadd_rn(off, prev);
+        int hit = 4;
+#pragma unroll
+        for (int e = 3; e >= 0; --e) {
+            const int p = 128 * r + 4 * lane + e;
+            if (p < N && w[e] > 0.0f) {
+                last = p > last ? p : last;
+                if (__fadd_rn(base, q[e]) > theta) hit = e;
+            }
+        }
+        const unsigned b = __ballot_sync(FULL, hit < 4);
+        if (b) {
+            const int wl = __ffs(b) - 1;
+            return 128 * r + 4 * wl + __shfl_sync(FULL, hit, wl);
+        }
+        off = __fadd_rn(off, __shfl_sync(FULL, S, 31));
+    }
+    return (int)__reduce_max_sync(FULL, (unsigned)(last + 1)) - 1;
+}
+
+// One warp's compact list of unvisited nodes (shared memory, 16-bit ids).
+struct Compact {
+    uint16_t *e;
+    int L, n;
+    __device__ __forceinline__ void init(int lane)
+    {
+        for (int j = lane; j < n; j += 32) e[j] = (uint16_t)j;
+        L = n;
+        __syncwarp();
+    }
+    // remove the node at slot j (Sec. 4.1): the last node takes its place
+    __device__ __forceinline__ void remove(int j, int lane)
+    {
+        if (lane == 0) {
+            if (j == L - 1) {
+                e[j] = (uint16_t)n;
+            } else {
+                const int last = e[L - 1];
+                e[j] = (uint16_t)last;
+                e[last] = (uint16_t)j;
+            }
+        }
+        --L;
+        __syncwarp();
+    }
+};
+
+// One whole-row tour under the variant (SEL: 0 reservoir sampling, 1
+// roulette wheel; CT: compact list, else the bitmask tabu tb).  `row0` is the
+// weight matrix: 1/choice_info for reservoir sampling, choice_info for the
+// roulette wheel.
+template <int SEL, bool CT, int TW>
+__device__ __forceinline__ void build_tour_var(const ConstructArgs &a, const float *row0, Tabu<TW> &tb,
+                                               Compact &cl, int lane, int ant, uint32_t it, int32_t *trow)
+{
+    uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
+    philox_rounds<0, 10>(s4, a.key0, a.key1);
+    const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
+    int cur = start, slot = start, twin = start;
+    if constexpr (CT) {
+        cl.init(lane);
+    } else {
+        tb.clear(lane);
+        tb.mark(lane, start);
+    }
+    for (int t = 1; t < a.n; ++t) {
+        if constexpr (CT) cl.remove(slot, lane);
+        const float *row = row0 + (size_t)cur * a.ld;
+        int next = -1, nslot = -1;
+        if constexpr (SEL == 1) {
+            uint4 r4 = make_uint4(0xFFFFFFFEu, (uint32_t)t, (uint32_t)ant, it);
+            philox_rounds<0, 10>(r4, a.key0, a.key1);
+            const float u = unit_open(r4.x);
+            if constexpr (CT) {
+                const uint16_t *e = cl.e;
+                auto x = [&](int p0, int N, float (&w)[4]) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) w[k] = p0 + k < N ? row[e[p0 + k]] : 0.0f;
+                };
+                nslot = rwm_pick(x, cl.L, u, lane);
+                next = nslot >= 0 ? (int)cl.e[nslot] : -1;
+            } else {
+                auto x = [&](int p0, int N, float (&w)[4]) {
+                    const uint32_t bits = (tb.word_of(p0 < N ? p0 : 0) >> (p0 & 31)) & 0xFu;
+                    const float4 v = p0 < N ? *reinterpret_cast<const float4 *>(row + p0)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    w[0] = p0 < N && !(bits & 1u) ? v.x : 0.0f;
+                    w[1] = p0 + 1 < N && !(bits & 2u) ? v.y : 0.0f;
+                    w[2] = p0 + 2 < N && !(bits & 4u) ? v.z : 0.0f;
+                    w[3] = p0 + 3 < N && !(bits & 8u) ? v.w : 0.0f;
+                };
+                next = rwm_pick(x, a.n, u, lane);
+            }
+        } else {
+            // reservoir sampling over the compact list, slot-keyed draws
+            uint32_t bk = 0, bv = 0xFFFFFFFFu, bs = 0;
+            for (int r = 0; 128 * r < cl.L; ++r) {
+                const int j0 = 128 * r + 4 * lane;
+                if (j0 >= cl.L) continue;
+                uint4 d4 = make_uint4(0x40000000u | (uint32_t)(32 * r + lane), (uint32_t)t, (uint32_t)ant, it);
+                philox_rounds<0, 10>(d4, a.key0, a.key1);
+                const uint32_t wd[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int j = j0 + k;
+                    if (j >= cl.L) break;
+                    const uint32_t v = cl.e[j];
+                    const uint32_t kk = ord_key(__fmul_rn(log2f(unit_open(wd[k])), row[v]));
+                    if (kk > bk || (kk == bk && v < bv)) {
+                        bk = kk;
+                        bv = v;
+                        bs = (uint32_t)j;
+                    }
+                }
+            }
+            const uint32_t mx = __reduce_max_sync(FULL, bk);
+            const uint32_t win = __reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+            const unsigned owner = __ballot_sync(FULL, bv == win && bk == mx);
+            next = mx ? (int)win : -1;
+            nslot = owner ? (int)__shfl_sync(FULL, bs, __ffs(owner) - 1) : -1;
+        }
+        if (next < 0) {  // no positive weight: cannot happen with tau_min > 0
+            if (lane == 0) atomicOr(&a.sc->err, ERR_NO_UNVISITED);
+            return;
+        }
+        if constexpr (!CT) tb.mark(lane, next);
+        twin = (lane == (t & 31)) ? next : twin;
+        if ((t & 31) == 31 || t == a.n - 1) store_window(trow, lane, t >> 5, t, twin);
+        cur = next;
+        slot = nslot;
+    }
+}
+
+template <int SEL, bool CT, bool STAGED, int TW>
+__global__ void __launch_bounds__(384, 1) k_construct_var(const ConstructArgs a, int cons_warps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t it = (uint32_t)a.iter[0];
+    const float *row0 = a.wmat;
+    size_t off = 0;
+    if constexpr (STAGED) {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.stage_w_bytes);
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (!stage_table(smem, a.wmat, a.stage_w_bytes, nullptr, nullptr, 0, bar, 0, &a.sc->err)) return;
+        row0 = reinterpret_cast<const float *>(smem);
+        off = (size_t)a.stage_w_bytes + 16;
+    }
+    Tabu<TW> tb;
+    tb.nw = (a.n + 31) >> 5;
+    Compact cl;
+    cl.n = a.n;
+    cl.L = a.n;
+    cl.e = nullptr;
+    if constexpr (CT) {
+        const size_t per = ((size_t)a.n * 2 + 15) & ~size_t(15);
+        cl.e = reinterpret_cast<uint16_t *>(smem + off + (size_t)warp * per);
+    } else {
+        if constexpr (TW == 0) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
+    }
+    const int stride = gridDim.x * cons_warps;
+    const int ant_end = a.ant_offset + a.m;
+    int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
+    for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride)
+        build_tour_var<SEL, CT, TW>(a, row0, tb, cl, lane, ant, it, tours_g + (size_t)ant * a.ld);
+}
+
 using KernelFn = void (*)(const ConstructArgs, int);
 
 // tw: tabu words per lane (1, 2, 4), or 0 for the shared-memory tabu
@@ -538,21 +758,37 @@ KernelFn pick_kernel(int mode, int staged, int tw)
     return table[(mode << 3) | (staged << 2) | ti];
 }
 
+// whole-row variants: (sel, ct) != (0, 0); TW 1 (n <= 1024) or 0 for the bitmask
+KernelFn pick_kernel_var(int sel, int ct, int staged, int tw)
+{
+    if (ct) {
+        if (sel) return staged ? k_construct_var<1, true, true, 1> : k_construct_var<1, true, false, 1>;
+        return staged ? k_construct_var<0, true, true, 1> : k_construct_var<0, true, false, 1>;
+    }
+    if (tw == 1) return staged ? k_construct_var<1, false, true, 1> : k_construct_var<1, false, false, 1>;
+    return staged ? k_construct_var<1, false, true, 0> : k_construct_var<1, false, false, 0>;
+}
+
 }  // namespace
 
 cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
                            ConstructPlan *plan)
 {
     const bool row = a.cl == 0;
+    const bool var = row && (a.sel != 0 || a.ct != 0);
     const int nw = (a.n + 31) / 32;
-    plan->tw = tabu_words(a.n);
+    plan->tw = var ? (a.n <= 1024 ? 1 : 0) : tabu_words(a.n);
+    // per-warp shared memory besides the table: the compact list, or the tabu
+    // bitmask when it does not live in registers
+    const size_t per_warp = (var && a.ct) ? (((size_t)a.n * 2 + 15) & ~size_t(15))
+                                          : (plan->tw ? 0 : (size_t)nw * sizeof(uint32_t));
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
     // staged: one CTA per SM (the table fills its shared memory) carrying
     // ceil(m / #SMs) ants, at most 12 warps; warps loop over further ants
     int w = (a.m + num_sms - 1) / num_sms;
     w = w < 1 ? 1 : (w > 12 ? 12 : w);
-    const size_t masks = plan->tw ? 0 : (size_t)w * nw * sizeof(uint32_t);
+    const size_t masks = (size_t)w * per_warp;
     const size_t need = table + 16 + masks;
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
@@ -566,9 +802,10 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->cons_warps = 4;
         plan->gen_warps = 0;
         plan->grid = (a.m + 3) / 4;
-        plan->smem = plan->tw ? 0 : (size_t)4 * nw * sizeof(uint32_t);
+        plan->smem = (size_t)4 * per_warp;
     }
-    KernelFn k = pick_kernel(row ? ROW : CAND, plan->staged, plan->tw);
+    KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan->staged, plan->tw)
+                     : pick_kernel(row ? ROW : CAND, plan->staged, plan->tw);
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
 }
@@ -598,7 +835,9 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
         b.stage_w_bytes = (uint32_t)((size_t)a.n * a.ld * sizeof(float));
         b.stage_c_bytes = 0;
     }
-    KernelFn k = pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw);
+    const bool var = a.cl == 0 && (a.sel != 0 || a.ct != 0);
+    KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan.staged, plan.tw)
+                     : pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw);
     k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();
 }

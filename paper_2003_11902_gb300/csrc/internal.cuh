@@ -195,6 +195,8 @@ struct ConstructArgs {
     Scalars *sc;
     uint32_t stage_w_bytes;    // bytes of the staged weight table (16-byte multiple)
     uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
+    int32_t sel;               // whole-row selection: 0 reservoir sampling, 1 roulette wheel
+    int32_t ct;                // whole-row tabu: 0 bitmask, 1 compact list
 };
 
 // One unit of batched construction: ants first .. first+count-1 of a colony.
@@ -233,6 +235,7 @@ struct ScoreArgs {
 
 struct UpdateArgs {
     int32_t n, ld, cl, fullrow, evaporate;
+    int32_t recip;     // whole-row mode: store 1/choice_info (reservoir sampling) or choice_info
     float persist;     // float(1 - rho)
     float alpha;
     const float *eb;   // [n][ld]

@@ -215,7 +215,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
                     if (j == succ || j == pred) x = fminf(__fadd_rn(x, delta), tmax);
                 }
                 const float w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
-                wv[c] = FULLROW ? __frcp_rn(w) : w;
+                wv[c] = (FULLROW && a.recip) ? __frcp_rn(w) : w;
             } else {
                 x = 0.0f;
                 wv[c] = 0.0f;

@@ -126,6 +126,10 @@ mmas_status validate(const mmas_instance *inst, const mmas_params *p)
     if (p->ant_offset < 0 || (long long)p->ant_offset + p->m > INT_MAX)
         return fail(nullptr, MMAS_EINVAL, "ant_offset must be >= 0 and ant_offset + m < 2^31");
     if (p->ls < 0 || p->ls > 2) return fail(nullptr, MMAS_EINVAL, "ls must be 0, 1 or 2");
+    if (p->selection < 0 || p->selection > 1) return fail(nullptr, MMAS_EINVAL, "selection must be 0 or 1");
+    if (p->tabu < 0 || p->tabu > 1) return fail(nullptr, MMAS_EINVAL, "tabu must be 0 or 1");
+    if ((p->selection || p->tabu) && p->cl != 0)
+        return fail(nullptr, MMAS_EINVAL, "selection and tabu variants are whole-row (cl = 0) variants");
     if (p->ls > 0 && p->cl < 1)
         return fail(nullptr, MMAS_EINVAL, "ls needs candidate lists (cl >= 1) as neighbour lists");
     if (inst->xy) {
@@ -271,6 +275,8 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ConstructArgs &ca = h->cargs;
     ca.n = n; ca.m = m; ca.cl = cl; ca.ld = ld; ca.fallback = h->p.fallback;
     ca.ant_offset = h->p.ant_offset;
+    ca.sel = h->p.selection;
+    ca.ct = h->p.tabu;
     ca.key0 = (uint32_t)(h->p.seed & 0xFFFFFFFFull);
     ca.key1 = (uint32_t)(h->p.seed >> 32);
     for (int r = 0; r < 10; ++r) {
@@ -308,6 +314,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
 
     UpdateArgs &ua = h->uargs;
     ua.n = n; ua.ld = ld; ua.cl = cl; ua.fullrow = cl == 0; ua.evaporate = 1;
+    ua.recip = cl == 0 && h->p.selection == 0;
     ua.persist = (float)(1.0 - (double)h->p.rho);
     ua.alpha = h->p.alpha;
     ua.eb = h->eb; ua.tau = h->tau; ua.wmat = h->wmat; ua.cand32 = h->cand32; ua.cwinv = h->cwinv;
@@ -358,6 +365,8 @@ void mmas_default_params(mmas_params *p)
     p->device = 0;
     p->ant_offset = 0;
     p->ls = 0;
+    p->selection = 0;
+    p->tabu = 0;
     p->stream = nullptr;
 }
 

@@ -48,7 +48,8 @@ class mmas_params(C.Structure):
     _fields_ = [("m", C.c_int32), ("alpha", C.c_float), ("beta", C.c_float), ("rho", C.c_float),
                 ("p_best", C.c_float), ("cl", C.c_int32), ("seed", C.c_uint64),
                 ("deposit", C.c_int32), ("fallback", C.c_int32), ("device", C.c_int32),
-                ("ant_offset", C.c_int32), ("ls", C.c_int32), ("stream", C.c_void_p)]
+                ("ant_offset", C.c_int32), ("ls", C.c_int32), ("selection", C.c_int32),
+                ("tabu", C.c_int32), ("stream", C.c_void_p)]
 
 
 class mmas_batch_config(C.Structure):
@@ -301,7 +302,7 @@ class Colony:
 
     def __init__(self, xy=None, dist=None, m=None, alpha=1.0, beta=2.0, rho=0.02, p_best=0.01,
                  cl=32, seed=1, deposit=0, fallback=0, device=0, ant_offset=0, ls=0,
-                 stream="torch"):
+                 selection=0, tabu=0, stream="torch"):
         p = mmas_default_params()
         n = (np.asarray(xy) if xy is not None else np.asarray(dist)).shape[0]
         p.m = int(m) if m is not None else n
@@ -309,6 +310,7 @@ class Colony:
         p.cl, p.seed, p.deposit, p.fallback, p.device = cl, int(seed), deposit, fallback, device
         p.ant_offset = int(ant_offset)
         p.ls = int(ls)
+        p.selection, p.tabu = int(selection), int(tabu)
         if stream == "torch":
             stream = _torch_stream()
         elif stream == 0:

@@ -33,9 +33,10 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layout_matches_header():
-    assert C.sizeof(mmas.mmas_params) == 64
+    assert C.sizeof(mmas.mmas_params) == 72
     assert mmas.mmas_params.seed.offset == 24
-    assert mmas.mmas_params.stream.offset == 56
+    assert mmas.mmas_params.selection.offset == 52
+    assert mmas.mmas_params.stream.offset == 64
     assert C.sizeof(mmas.mmas_instance) == 24
     assert C.sizeof(mmas.mmas_batch_config) == 8
 
@@ -50,6 +51,7 @@ def test_default_params(lib):
     ("rho", 0.0, "rho"), ("rho", 1.0, "rho"), ("p_best", 1.0, "p_best"), ("alpha", -1.0, "alpha"),
     ("beta", float("nan"), "beta"), ("cl", 33, "cl"), ("cl", -1, "cl"), ("m", -5, "m must"),
     ("deposit", 2, "deposit"), ("fallback", 3, "fallback"), ("ls", 3, "ls"),
+    ("selection", 2, "selection"), ("tabu", -1, "tabu"),
 ])
 def test_bad_parameters_are_rejected_before_device_work(lib, field, value, needle):
     p = mmas.mmas_default_params()
@@ -126,3 +128,10 @@ def test_batch_instance_checks(lib):
     # colony 0 fails its own validation: the message names it
     with pytest.raises(mmas.MMASError, match="colony 0: n must be"):
         mmas.mmas_batch_create([(instances.uniform(2, 1), None), (instances.uniform(30, 2), None)], p)
+
+
+def test_whole_row_variants_need_whole_rows(lib):
+    p = mmas.mmas_default_params()
+    p.cl, p.selection = 8, 1
+    with pytest.raises(mmas.MMASError, match="whole-row"):
+        mmas.mmas_create(xy=instances.uniform(50, 1), params=p)
