@@ -45,6 +45,11 @@ WORKLOADS = {
     # name: (n, m, cl, instance kind, instance seed)
     "uniform-n1000-cl32": dict(n=1000, m=1000, cl=32, kind="uniform", iseed=1001),
     "uniform-n200-fullrow": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002),
+    # the same whole-row workload under the paper's other selection / tabu variants
+    "uniform-n200-fullrow-rwm": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002, selection=1),
+    "uniform-n200-fullrow-rwm-ct": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002, selection=1,
+                                        tabu=1),
+    "uniform-n200-fullrow-ct": dict(n=200, m=200, cl=0, kind="uniform", iseed=1002, tabu=1),
     "clustered-n3800-cl16-2opt": dict(n=3800, m=1000, cl=16, kind="clustered", iseed=1003, ls=1),
     # 256 uniform instances, n = round(exp(U[ln 100, ln 2000])) (size seed 1000), coordinate
     # seed 1000 + i, m = n each
@@ -58,6 +63,8 @@ WORKLOADS = {
                                           train_steps=40, lr=2e-3, race_s=1.5),
 }
 DEFAULT_STEPS = {"uniform-n1000-cl32": 1000, "uniform-n200-fullrow": 1000,
+                 "uniform-n200-fullrow-rwm": 1000, "uniform-n200-fullrow-rwm-ct": 1000,
+                 "uniform-n200-fullrow-ct": 1000,
                  "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30,
                  "learned-prior-n1000-cl16-2opt": 200}
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
@@ -90,6 +97,11 @@ def _batch_cfg(w, xys):
     return {"colonies": w["count"], "n": f"log-uniform [{w['lo']}, {w['hi']}]", "n_min": min(ns),
             "n_max": max(ns), "total_ants": sum(ns), "m": "n per colony", "cl": w["cl"],
             "instance": "uniform, size seed 1000, coordinate seed 1000 + i", **PARAMS}
+
+
+def _variant(w):
+    """Whole-row selection / tabu variant of a workload (both 0 by default)."""
+    return {"selection": w.get("selection", 0), "tabu": w.get("tabu", 0)}
 
 
 def _peaks():
@@ -182,7 +194,7 @@ def cpu_baseline(w, xy, budget_s=12.0):
     """The oracle as it stands, all host cores, whole iterations until budget_s."""
     import oracle as O
     cores = os.cpu_count() or 1
-    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **PARAMS)
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **_variant(w), **PARAMS)
     it, t0 = 0, time.perf_counter()
     while True:
         col.iterate(1, threads=cores)
@@ -203,7 +215,7 @@ def run_reference(args, w):
     import oracle as O
     xy = _instance(w)
     cores = os.cpu_count() or 1
-    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **PARAMS)
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, ls=w.get("ls", 0), **_variant(w), **PARAMS)
     t0 = time.perf_counter()
     col.iterate(1, threads=cores)
     t_iter = time.perf_counter() - t0
@@ -254,6 +266,9 @@ def _cfg(w):
          **PARAMS}
     if w.get("ls"):
         c["local_search"] = "2-opt of the iteration best" if w["ls"] == 1 else "2-opt of every ant"
+    if w.get("cl") == 0:
+        c["selection"] = "roulette wheel" if w.get("selection") else "weighted reservoir sampling"
+        c["tabu"] = "compact list" if w.get("tabu") else "bitmask"
     return c
 
 
@@ -316,7 +331,7 @@ def run_ours(args, w):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)  # the flush, the colony and all timing share this stream
     col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, ls=w.get("ls", 0),
-                 stream=stream.cuda_stream, **PARAMS)
+                 stream=stream.cuda_stream, **_variant(w), **PARAMS)
     col.enable_phase_timing(True)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -353,7 +368,7 @@ def run_ours(args, w):
     e2e_total = 0.0
     t0 = time.perf_counter()
     col2 = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, ls=w.get("ls", 0),
-                  stream=stream.cuda_stream, **PARAMS)
+                  stream=stream.cuda_stream, **_variant(w), **PARAMS)
     col2.synchronize()
     e2e_total += time.perf_counter() - t0
     for _ in range(args.steps):
