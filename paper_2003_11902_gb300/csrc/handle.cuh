@@ -29,6 +29,10 @@ struct mmas_handle {
     int *maxd = nullptr;
     int32_t *ext_tour = nullptr, *ext_len = nullptr;
     int32_t *nnd = nullptr;
+    int32_t xe = 0;                  // reach-list length of the greedy fallback (0: none)
+    int32_t *xl32 = nullptr;         // [n][xe]
+    uint2 *xlw = nullptr;            // [n][xe]
+    float *xlb = nullptr;            // [n]
     mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
 
     mmas::ConstructArgs cargs{};

@@ -197,7 +197,18 @@ struct ConstructArgs {
     uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
     int32_t sel;               // whole-row selection: 0 reservoir sampling, 1 roulette wheel
     int32_t ct;                // whole-row tabu: 0 bitmask, 1 compact list
+    // greedy-fallback reach list (candidate-list mode, fallback 0; xe = 0: none,
+    // else xe <= REACH_MAX):
+    // per row the xe nearest nodes with this iteration's choice_info, and a
+    // bound on the choice_info of every node outside the list
+    int32_t xe;
+    const uint2 *xlw;          // [n][xe] {float bits of choice_info, node}
+    const float *xlb;          // [n]
 };
+
+// Longest reach list of the greedy fallback (lane l of a warp holds entries
+// l, l + 32, l + 64, l + 96).
+constexpr int REACH_MAX = 128;
 
 // One unit of batched construction: ants first .. first+count-1 of a colony.
 struct BatchChunk {
@@ -245,6 +256,11 @@ struct UpdateArgs {
     float *cwinv;      // [n][cl]
     const int2 *nbr;   // [n] or nullptr (no deposit)
     Scalars *sc;
+    // greedy-fallback reach list, refreshed with choice_info (xe = 0: none)
+    int32_t xe;
+    const int32_t *xl32;  // [n][xe] the xe nearest nodes of each row, (d, id) order
+    uint2 *xlw;           // [n][xe] {float bits of choice_info, node}
+    float *xlb;           // [n] max choice_info over j != i with eta^beta_ij <= that of the last listed node
 };
 
 // Message returned by mmas_last_error(NULL) on the calling thread.

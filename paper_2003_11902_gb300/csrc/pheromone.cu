@@ -184,10 +184,22 @@ __global__ void __launch_bounds__(256)
 // Row i of the fused pass: evaporate with both clamps, deposit on the row's
 // two tour edges, write choice_info (or its reciprocal), then gather
 // 1/choice_info of the row's candidates.  The whole CTA works on the row.
+// With a reach list (xe > 0) the pass also gathers the listed nodes'
+// choice_info and takes the row's largest choice_info among the nodes j != i
+// whose eta^beta does not exceed the last listed node's: every node outside
+// the list is among them (eta^beta does not increase with distance beyond the
+// list), so this bounds their choice_info for the greedy fallback.
 template <bool FULLROW, bool ALPHA1>
 __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmin, float tmax,
                                            float delta)
 {
+    __shared__ uint32_t s_bound[8];
+    const bool reach = !FULLROW && a.xe > 0;
+    // no node lies outside a list of all n - 1 others
+    const float thr = (reach && a.xe < a.n - 1)
+                          ? __ldg(a.eb + (size_t)i * a.ld + a.xl32[(size_t)i * a.xe + a.xe - 1])
+                          : -1.0f;
+    float bound = 0.0f;
     const int nq = a.ld >> 2;
     int succ = -1, pred = -1;
     if (a.nbr) {
@@ -216,6 +228,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
                 }
                 const float w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
                 wv[c] = (FULLROW && a.recip) ? __frcp_rn(w) : w;
+                if (!FULLROW && j != i && ev[c] <= thr) bound = fmaxf(bound, w);
             } else {
                 x = 0.0f;
                 wv[c] = 0.0f;
@@ -226,11 +239,27 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
         wrow[q] = make_float4(wv[0], wv[1], wv[2], wv[3]);
     }
     if (!FULLROW && a.cl > 0) {
+        if (reach) {  // choice_info >= 0: its bits order like the values
+            const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
+            if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = wmax;
+        }
         __syncthreads();  // this row's choice_info is written and visible to the CTA
         const float *w1 = a.wmat + (size_t)i * a.ld;
         for (int c = threadIdx.x; c < a.cl; c += blockDim.x) {
             const int v = a.cand32[(size_t)i * a.cl + c];
             a.cwinv[(size_t)i * a.cl + c] = __frcp_rn(w1[v]);
+        }
+        if (reach) {
+            for (int e = threadIdx.x; e < a.xe; e += blockDim.x) {
+                const int v = a.xl32[(size_t)i * a.xe + e];
+                a.xlw[(size_t)i * a.xe + e] = make_uint2(__float_as_uint(w1[v]), (uint32_t)v);
+            }
+            if (threadIdx.x == 0) {
+                uint32_t m = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_bound[w] > m ? s_bound[w] : m;
+                a.xlb[i] = __uint_as_float(m);
+            }
+            __syncthreads();  // s_bound is read before the CTA's next row writes it
         }
     }
 }

@@ -67,7 +67,8 @@ void free_all(mmas_handle *h)
         if (e) cudaEventDestroy(e);
     void *bufs[] = {h->xy,      h->dist,   h->eb,      h->tau,     h->wmat, h->cwinv,
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
-                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->nnd};
+                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->nnd,
+                    h->xl32,    h->xlw,    h->xlb};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -268,6 +269,16 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
 
     CK(h, launch_eta_beta(h->dist, n, ld, (double)h->p.beta, h->eb, s));
     CK(h, launch_candidates(h->dist, n, ld, cl, h->cand32, h->cand16, s));
+    // greedy fallback (fallback 0): a reach list of the min(REACH_MAX, n - 1)
+    // nearest nodes per row, refreshed with choice_info, usually decides it
+    // without a row scan
+    if (cl > 0 && h->p.fallback == 0 && n - 1 > cl) {
+        h->xe = n - 1 < REACH_MAX ? n - 1 : REACH_MAX;
+        CK(h, dalloc(&h->xl32, (size_t)n * h->xe * sizeof(int32_t), h->stream));
+        CK(h, dalloc(&h->xlw, (size_t)n * h->xe * sizeof(uint2), h->stream));
+        CK(h, dalloc(&h->xlb, (size_t)n * sizeof(float), h->stream));
+        CK(h, launch_candidates(h->dist, n, ld, h->xe, h->xl32, nullptr, s));
+    }
     CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, s));
     CK(h, launch_init_colony(n, ld, (double)h->p.rho, h->p_root, h->tau, h->sc, s));
 
@@ -286,6 +297,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.iter = &h->sc->iter;
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
     ca.tours = h->tours; ca.sc = h->sc;
+    ca.xe = h->xe; ca.xlw = h->xlw; ca.xlb = h->xlb;
     ca.stage_w_bytes = (uint32_t)cw_bytes;
     ca.stage_c_bytes = (uint32_t)cc_bytes;
     if (cl == 0) { ca.stage_w_bytes = 0; ca.stage_c_bytes = 0; }
@@ -319,6 +331,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ua.alpha = h->p.alpha;
     ua.eb = h->eb; ua.tau = h->tau; ua.wmat = h->wmat; ua.cand32 = h->cand32; ua.cwinv = h->cwinv;
     ua.nbr = h->nbr; ua.sc = h->sc;
+    ua.xe = h->xe; ua.xl32 = h->xl32; ua.xlw = h->xlw; ua.xlb = h->xlb;
 
     // choice_info of the initial pheromone
     UpdateArgs refresh = ua;

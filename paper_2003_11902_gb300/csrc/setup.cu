@@ -86,7 +86,7 @@ __global__ void k_candidates(const int32_t *__restrict__ d, int32_t n, int32_t l
             best = warp_min_u64(best);
             if (lane == 0) {
                 cand32[(size_t)i * cl + r] = (int32_t)(best & 0xFFFFFFFFull);
-                cand16[(size_t)i * cl + r] = (uint16_t)(best & 0xFFFFull);
+                if (cand16) cand16[(size_t)i * cl + r] = (uint16_t)(best & 0xFFFFull);
             }
             last = best;
         }

@@ -124,6 +124,40 @@ def test_first_iteration_tours_match_oracle(n, m, cl, fb, src):
     g.close()
 
 
+@pytest.mark.parametrize("n,cl,kind", [(700, 6, "uniform"), (1500, 8, "clustered"),
+                                       (5000, 8, "clustered")])
+def test_greedy_fallback_after_deposits_matches_oracle(n, cl, kind):
+    """Short candidate lists after deposits on long random tours: the greedy
+    fallback runs often, and on rows where a far node's choice_info beats every
+    unvisited near one it cannot be decided from the reach list of the 128
+    nearest nodes, so both the reach-list decision and the row scan are taken."""
+    xy = I.clustered(n, 40 + n) if kind == "clustered" else I.uniform(n, 40 + n)
+    m = 32
+    g, o = _pair(xy=xy, m=m, cl=cl, rho=0.05, seed=7)
+    d = o.state()["d"]
+    for r in range(12):
+        tour = I.random_permutation(n, 500 + r) if r % 3 else O.nn_tour(d)[1]
+        length = int(O.tour_length(d, tour))
+        g.update(tour, length)
+        o.update(tour, length)
+    tau, _, _ = g.pheromone()
+    np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
+    it = o.iteration  # the oracle's update advanced it; the draws of both follow it
+    g.set_iteration(it)
+    g.construct()
+    tours, lens = g.tours()
+    kinds = []
+    for k in range(m):
+        assert is_permutation(tours[k], n)
+        kinds.append(check_ant(o, it, k, tours[k], lens[k]))
+    fb = g.stats()["fallback_steps"]
+    near = kinds.count("near_tie")
+    print(f"n={n} cl={cl} {kind}: {fb} fallback steps in {m} tours, {near} near-tie divergences")
+    assert fb > m
+    assert near <= max(1, m // 50)
+    g.close()
+
+
 def test_lockstep_iterations_match_oracle():
     """Whole-run parity: as long as every pick agrees, tours, lengths, limits,
     best tour and pheromone agree after every iteration."""
