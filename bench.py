@@ -41,6 +41,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+_PRIOR_TRAIN = dict(train_count=256, train_seed=2000, train_iters=30, train_steps=8, lr=2e-3)
 WORKLOADS = {
     # name: (n, m, cl, instance kind, instance seed)
     "uniform-n1000-cl32": dict(n=1000, m=1000, cl=32, kind="uniform", iseed=1001),
@@ -56,17 +57,23 @@ WORKLOADS = {
     "batched-256-n100-2000-cl32": dict(kind="batched", count=256, lo=100, hi=2000, cl=32,
                                        size_seed=1000),
     # the learned edge prior: trained on elite tours of generated instances (n log-uniform in
-    # [200, 2000], coordinate seeds 5000 + i), then plain and prior MMAS raced on the n = 1000
-    # instance (cl = 16, 2-opt of the iteration best) for equal wall time
+    # [200, 2000], size seed 2000, coordinate seeds 5000 + i; each instance's colony run in
+    # batches of 256 for train_iters iterations gives its elite tour), then plain and prior
+    # MMAS (m = n, cl = 16, 2-opt of the iteration best) raced for equal wall time on a uniform
+    # instance of n = 1000, 5000 or 18500
     "learned-prior-n1000-cl16-2opt": dict(kind="prior", n=1000, m=1000, cl=16, iseed=1001, ls=1,
-                                          train_count=16, train_seed=2000, train_iters=40,
-                                          train_steps=40, lr=2e-3, race_s=1.5),
+                                          **_PRIOR_TRAIN, race_s=2.0),
+    "learned-prior-n5000-cl16-2opt": dict(kind="prior", n=5000, m=5000, cl=16, iseed=1005, ls=1,
+                                          **_PRIOR_TRAIN, race_s=6.0),
+    "learned-prior-n18500-cl16-2opt": dict(kind="prior", n=18500, m=18500, cl=16, iseed=1018, ls=1,
+                                           **_PRIOR_TRAIN, race_s=15.0),
 }
 DEFAULT_STEPS = {"uniform-n1000-cl32": 1000, "uniform-n200-fullrow": 1000,
                  "uniform-n200-fullrow-rwm": 1000, "uniform-n200-fullrow-rwm-ct": 1000,
                  "uniform-n200-fullrow-ct": 1000,
                  "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30,
-                 "learned-prior-n1000-cl16-2opt": 200}
+                 "learned-prior-n1000-cl16-2opt": 200, "learned-prior-n5000-cl16-2opt": 30,
+                 "learned-prior-n18500-cl16-2opt": 10}
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
 # kernels in one iteration graph: construct, score, update; with 2-opt of the
 # iteration best also the 2-opt and the best/limits kernel; with 2-opt of every
@@ -205,6 +212,29 @@ def cpu_baseline(w, xy, budget_s=12.0):
     return {"value": w["m"] * it / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{it} whole iterations (all {w['m']} ants + pheromone update) of the "
                       f"same workload, OpenMP over ants on {cores} threads, {el:.1f} s"}
+
+
+def cpu_baseline_sample(w, xy, budget_s=12.0):
+    """The oracle as it stands, all host cores, for instances whose whole
+    iterations outlast the budget: ants of one iteration constructed in parallel
+    until budget_s (set-up untimed)."""
+    import concurrent.futures as cf
+
+    import oracle as O
+    cores = os.cpu_count() or 1
+    col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], seed=1, **PARAMS)
+    it, done, t0 = col.iteration, 0, time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        while done < w["m"]:
+            ants = range(done, min(done + cores, w["m"]))
+            list(ex.map(lambda k: col.construct(it, int(k)), ants))
+            done += len(ants)
+            if time.perf_counter() - t0 >= budget_s:
+                break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {w['m']} ants of one iteration constructed (construction only: no "
+                      f"local search or pheromone update; set-up untimed), {cores} threads, {el:.1f} s"}
 
 
 def run_reference(args, w):
@@ -617,6 +647,33 @@ def _race(col, seconds, target, check_every=5):
     return trace, hit
 
 
+def _train_prior(prior, w, count, dev, stream):
+    """Train `prior` on the elite tours of `count` generated instances: each
+    chunk of 256 runs as one batch of colonies (m = n) for train_iters
+    iterations, then every colony's best tour drives train_steps Adam steps on
+    that colony.  Returns the wall time and the mean first / last loss per chunk."""
+    from paper_2003_11902_gb300 import Batch
+    from paper_2003_11902_gb300 import instances as I
+
+    sizes = I.log_uniform_sizes(count, w["train_seed"], 200, 2000)
+    t0 = time.perf_counter()
+    by_chunk = []
+    for c0 in range(0, count, 256):
+        xys = [I.uniform(int(n), 5000 + c0 + i) for i, n in enumerate(sizes[c0:c0 + 256])]
+        bt = Batch(xys=xys, m=0, cl=w["cl"], seed=100 + c0, device=dev, stream=stream, **PARAMS)
+        bt.iterate(w["train_iters"])
+        first, last = [], []
+        for c in range(len(xys)):
+            _, elite = bt.best_tour(c)
+            col = bt.colony(c)
+            first.append(prior.train(col, elite, steps=1, lr=w["lr"]))
+            last.append(prior.train(col, elite, steps=w["train_steps"] - 1, lr=w["lr"]))
+            col.close()
+        bt.close()
+        by_chunk.append((round(float(np.mean(first)), 4), round(float(np.mean(last)), 4)))
+    return time.perf_counter() - t0, sizes, by_chunk
+
+
 def run_ours_prior(args, w):
     import torch
 
@@ -631,35 +688,41 @@ def run_ours_prior(args, w):
     common = dict(cl=w["cl"], device=dev, ls=w["ls"], stream=stream.cuda_stream, **PARAMS)
     # ---- training on elite tours of generated instances
     prior = Prior(I.prior_params(1), device=dev)
-    sizes = I.log_uniform_sizes(w["train_count"], w["train_seed"], 200, 2000)
-    t0 = time.perf_counter()
-    losses = []
-    for i, n in enumerate(sizes):
-        col = Colony(xy=I.uniform(int(n), 5000 + i), m=int(n), seed=100 + i, **common)
-        col.iterate(w["train_iters"])
-        _, elite = col.best_tour()
-        first = prior.train(col, elite, steps=1, lr=w["lr"])
-        last = prior.train(col, elite, steps=w["train_steps"] - 1, lr=w["lr"])
-        losses.append((round(first, 4), round(last, 4)))
-        col.close()
-    train_s = time.perf_counter() - t0
+    count = args.train_instances or w["train_count"]
+    train_s, sizes, by_chunk = _train_prior(prior, w, count, dev, stream.cuda_stream)
     # ---- equal-wall-time race on the evaluation instance
     xy = _instance(w)
-    path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
-    with open(path) as f:
-        lstar = json.load(f)["lstar"]
-    target = 1.02 * lstar
+    lstar = None
+    if w["n"] == 1000:
+        path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
+        with open(path) as f:
+            lstar = json.load(f)["lstar"]
+    # three colonies: plain eta^beta, eta^beta replaced by the edge
+    # probabilities, and eta^beta weighted by them (gamma = 1)
     plain = Colony(xy=xy, m=w["m"], seed=1, **common)
+    weighted = Colony(xy=xy, m=w["m"], seed=1, **common)
     guided = Colony(xy=xy, m=w["m"], seed=1, **common)
     t0 = time.perf_counter()
     prior.apply(guided)
     apply_s = time.perf_counter() - t0
-    plain.iterate(2)
-    guided.iterate(2)
+    prior.apply_weighted(weighted, 1.0)
     race = {}
-    for name, col in (("plain", plain), ("prior", guided)):
-        trace, hit = _race(col, w["race_s"], target)
-        race[name] = {"best_at_end": trace[-1][1], "seconds_to_2pct": hit, "trace": trace[::4]}
+    for name, col in (("plain", plain), ("prior", guided), ("prior_weighted", weighted)):
+        col.iterate(2)
+        trace, _ = _race(col, w["race_s"], 0)
+        race[name] = {"best_at_end": trace[-1][1], "trace": trace}
+    weighted.close()
+    # the time each colony first came within 2% of the target: L* (the
+    # oracle's long-run best) where it is known, else the better final best
+    # of the two colonies
+    if lstar is not None:
+        target, target_source = 1.02 * lstar, "1.02 L*, L* from tests/golden/lstar_uniform_n1000.json (oracle)"
+    else:
+        target = 1.02 * min(r["best_at_end"] for r in race.values())
+        target_source = "1.02 x the better final best of the two colonies (no oracle L* at this size)"
+    for r in race.values():
+        r["seconds_to_target"] = next((t for t, b in r["trace"] if b <= target), None)
+        r["trace"] = r["trace"][::max(1, len(r["trace"]) // 40)]
     plain.close()
     # ---- throughput of the prior-guided colony (as for the other workloads)
     guided.enable_phase_timing(True)
@@ -716,14 +779,15 @@ def run_ours_prior(args, w):
         "gpu_launches": KERNELS_PER_ITERATION[w["ls"]] * args.steps,
         "clocks": clocks,
         "learned_prior": {
-            "train_instances": len(sizes), "train_sizes": [int(x) for x in sizes],
-            "train_s": round(train_s, 3), "loss_first_last": losses, "apply_s": round(apply_s, 4),
-            "race_seconds": w["race_s"], "target": target, "lstar": lstar,
-            "lstar_source": "tests/golden/lstar_uniform_n1000.json (oracle, cl = 32, no local search)",
-            "race": race},
+            "train_instances": len(sizes), "train_n_range": [int(sizes.min()), int(sizes.max())],
+            "train_iters": w["train_iters"], "train_steps": w["train_steps"],
+            "train_s": round(train_s, 3), "loss_first_last_per_256": by_chunk,
+            "apply_s": round(apply_s, 4), "race_seconds": w["race_s"], "target": target,
+            "target_source": target_source, "race": race},
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(dict(w, m=w["m"]), xy)
+        cb = cpu_baseline if w["n"] <= 2000 else cpu_baseline_sample
+        line["cpu_baseline"] = cb(dict(w, m=w["m"]), xy)
         line["cpu_baseline"]["sample"] += " (plain MMAS: the oracle has no learned prior)"
     print(json.dumps(line), flush=True)
 
@@ -738,6 +802,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform-n1000-cl32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gap", action="store_true", help="skip the time-to-2%%-gap run")
+    ap.add_argument("--train-instances", type=int, default=None,
+                    help="learned-prior workloads: generated training instances (default 256)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -83,8 +83,8 @@ typedef struct {
  *            iteration best; 2 2-opt every ant's tour.  Bentley's 2-opt with
  *            the candidate lists as neighbour lists and don't-look bits, first
  *            improvement, cities visited in index order, runs repeated until
- *            one makes no move.  Needs cl >= 1 and 13n bytes of shared memory
- *            per CTA (n <= 17,800 on GB300)                          (0)
+ *            one makes no move.  Needs cl >= 1 and 12.125n bytes + 2 KB of
+ *            shared memory per CTA (n <= 19,000 on GB300)             (0)
  *   selection  whole-row mode (cl = 0) only: 0 weighted reservoir sampling
  *            (Alg. 4); 1 the parallel roulette wheel (Sec. 4.2.1), one draw
  *            per step, the exact single-precision procedure described below (0)
@@ -301,6 +301,11 @@ mmas_status mmas_prior_grad(mmas_prior *p, mmas_handle *h, const int32_t *tour, 
  * candidate's d^-beta).  Then choice_info is refreshed from the current
  * pheromone.  The colony's pheromone, limits and iteration index are unchanged. */
 mmas_status mmas_prior_apply(mmas_prior *p, mmas_handle *h);
+/* Weight instead of replace: eta^beta of the 16 candidate edges of row i is
+ * multiplied by sigmoid(s[i][k])^gamma, every other entry of the row by
+ * (min_k sigmoid(s[i][k]))^gamma; gamma = 0 leaves plain MMAS, 0 <= gamma <= 64.
+ * Then choice_info is refreshed as by mmas_prior_apply.  Errors as there. */
+mmas_status mmas_prior_apply_weighted(mmas_prior *p, mmas_handle *h, float gamma);
 void mmas_prior_destroy(mmas_prior *p);
 const char *mmas_prior_last_error(const mmas_prior *p);
 
@@ -351,6 +356,13 @@ mmas_status mmas_batch_best_lengths(mmas_batch *b, int32_t *lens_out);
 /* Synchronise; copy colony c's last tours (m_c x n_c) and lengths (m_c).
  * Either pointer may be NULL. */
 mmas_status mmas_batch_get_tours(mmas_batch *b, int32_t colony, int32_t *tours, int32_t *lens);
+
+/* Colony c as an ordinary handle (*out), owned by the batch: valid until
+ * mmas_batch_destroy and never passed to mmas_destroy.  Every other call that
+ * takes a handle accepts it (a learned prior trains on and applies to it, for
+ * instance); batch iterations and calls on the handle advance the same colony.
+ * Errors: EINVAL (bad colony index, NULL out). */
+mmas_status mmas_batch_colony(mmas_batch *b, int32_t colony, mmas_handle **out);
 
 /* Use launch shape *cfg for the construction (re-records the graph). */
 mmas_status mmas_batch_set_config(mmas_batch *b, const mmas_batch_config *cfg);

@@ -444,6 +444,14 @@ mmas_status mmas_batch_get_tours(mmas_batch *b, int32_t colony, int32_t *tours, 
     return MMAS_OK;
 }
 
+mmas_status mmas_batch_colony(mmas_batch *b, int32_t colony, mmas_handle **out)
+{
+    if (check_batch(b) || check_colony(b, colony)) return MMAS_EINVAL;
+    if (!out) return bfail(b, MMAS_EINVAL, "out must be non-NULL");
+    *out = b->col[colony];
+    return MMAS_OK;
+}
+
 mmas_status mmas_batch_set_config(mmas_batch *b, const mmas_batch_config *cfg)
 {
     if (check_batch(b)) return MMAS_EINVAL;

@@ -272,6 +272,31 @@ __global__ void k_prior_apply(const float *s, const int32_t *nn, int n, int ld, 
     }
 }
 
+// eta^beta <- eta^beta sigmoid(s)^gamma on each row's candidate edges and
+// eta^beta (min_k sigmoid(s_ik))^gamma elsewhere (the distance order among
+// the other entries is kept).
+__global__ void k_prior_weight(const float *s, const int32_t *nn, int n, int ld, float gamma, float *eb)
+{
+    __shared__ float s_scale;
+    __shared__ float s_cand[KN];
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        float *row = eb + (size_t)i * ld;
+        if (threadIdx.x == 0) {
+            float pmin = 1.0f;
+            for (int k = 0; k < KN; ++k) pmin = fminf(pmin, sigmoidf_(s[i * KN + k]));
+            s_scale = powf(pmin, gamma);
+        }
+        if (threadIdx.x < KN)
+            s_cand[threadIdx.x] = row[nn[i * KN + threadIdx.x]] * powf(sigmoidf_(s[i * KN + threadIdx.x]), gamma);
+        __syncthreads();
+        const float sc = s_scale;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] *= sc;
+        __syncthreads();
+        if (threadIdx.x < KN) row[nn[i * KN + threadIdx.x]] = s_cand[threadIdx.x];
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 struct mmas_prior {
@@ -628,6 +653,24 @@ mmas_status mmas_prior_apply(mmas_prior *p, mmas_handle *h)
     cudaStream_t s = h->stream;
     PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, s));
     k_prior_apply<<<std::min(h->n, 4096), 256, 0, s>>>(p->s, p->nn, h->n, h->ld, h->eb);
+    PCK(p, cudaGetLastError());
+    UpdateArgs refresh = h->uargs;
+    refresh.evaporate = 0;
+    refresh.nbr = nullptr;
+    PCK(p, launch_update(refresh, h->num_sms, s));
+    return check_err(p, s);
+}
+
+mmas_status mmas_prior_apply_weighted(mmas_prior *p, mmas_handle *h, float gamma)
+{
+    if (!p) return pfail(nullptr, MMAS_EINVAL, "prior is NULL");
+    if (!(gamma >= 0.0f) || gamma > 64.0f) return pfail(p, MMAS_EINVAL, "gamma must be in [0, 64]");
+    mmas_status st = check_colony_for_prior(p, h);
+    if (st != MMAS_OK) return st;
+    if ((st = forward(p, h)) != MMAS_OK) return st;
+    cudaStream_t s = h->stream;
+    PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, s));
+    k_prior_weight<<<std::min(h->n, 4096), 256, 0, s>>>(p->s, p->nn, h->n, h->ld, gamma, h->eb);
     PCK(p, cudaGetLastError());
     UpdateArgs refresh = h->uargs;
     refresh.evaporate = 0;

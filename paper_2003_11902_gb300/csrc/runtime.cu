@@ -316,8 +316,8 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ta.n = n; ta.m = m; ta.ld = ld; ta.k = cl;
     ta.nn = h->cand32; ta.nn16 = h->cand16; ta.xy = h->xy; ta.dist = h->dist; ta.tours = h->tours; ta.lens = h->lens;
     ta.err = &h->sc->err;
-    if (h->p.ls > 0 && two_opt_smem(n, cl, false) > (size_t)h->smem_optin)
-        return fail(h, MMAS_EINVAL, "ls needs 13n bytes of shared memory per CTA: n is too large");
+    if (h->p.ls > 0 && !two_opt_fits(n, cl, false, (size_t)h->smem_optin))
+        return fail(h, MMAS_EINVAL, "ls needs about 12.1n bytes of shared memory per CTA: n is too large");
     if (h->p.ls > 0) {
         CK(h, dalloc(&h->nnd, (size_t)n * cl * sizeof(int32_t), h->stream));
         CK(h, launch_neighbour_dist(ta, h->nnd, s));

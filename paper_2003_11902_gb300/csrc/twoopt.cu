@@ -65,8 +65,8 @@ struct Layout {
         off += 4u * n;
         L.pos = off;
         off += 4u * n;
-        L.dlb = off;
-        off += n;
+        L.dlb = off;  // don't-look bits, one per city
+        off += 4u * ((n + 31u) / 32u);
         L.total = off + 16u;
         return L;
     }
@@ -188,29 +188,48 @@ __device__ __forceinline__ void reverse_path(const TourView &tv, int pa, int pb,
     }
 }
 
+// Don't-look bits: bit c & 31 of word c >> 5.
+__device__ __forceinline__ bool dlb_get(const uint32_t *dlb, int c) { return (dlb[c >> 5] >> (c & 31)) & 1u; }
+
+// Set the bits of cities [lo, hi); thread t of `count` takes words t, t + count,
+// ... of the range, so no word has two writers.
+__device__ __forceinline__ void dlb_set_range(uint32_t *dlb, int lo, int hi, int t, int count)
+{
+    if (hi <= lo) return;
+    const int q0 = lo >> 5, q1 = (hi - 1) >> 5;
+    for (int q = q0 + t; q <= q1; q += count) {
+        const int b0 = q == q0 ? (lo & 31) : 0;
+        const int b1 = q == q1 ? ((hi - 1) & 31) : 31;
+        const uint32_t upto = b1 == 31 ? 0xFFFFFFFFu : ((1u << (b1 + 1)) - 1u);
+        dlb[q] |= upto & ~((1u << b0) - 1u);
+    }
+}
+
+__device__ __forceinline__ void dlb_clear(uint32_t *dlb, int c) { dlb[c >> 5] &= ~(1u << (c & 31)); }
+
 // After the reversal of [pa..pb]: the two added edges border the path, and its
 // two ends with their outer neighbours are the move's four cities, whose
 // don't-look bits clear.  Whichever of the two paths was reversed, the edge
 // before it is c1-c2 (successor side) or pred(c1)-pred(c2) (predecessor
 // side), and the edge after it the other one.
-__device__ __forceinline__ void finish_move(const TourView &tv, unsigned char *dlb, const Move &mv,
+__device__ __forceinline__ void finish_move(const TourView &tv, uint32_t *dlb, const Move &mv,
                                             int pa, int pb)
 {
     const int ia = tv.prv(pa), ib = tv.nxt(pb);
     tv.edge[ia] = mv.side ? mv.d34 : mv.d12;
     tv.edge[pb] = mv.side ? mv.d12 : mv.d34;
     const int u = tv.tour[ia], v = tv.tour[pa], x = tv.tour[pb], y = tv.tour[ib];
-    dlb[u] = 0; dlb[v] = 0; dlb[x] = 0; dlb[y] = 0;
+    dlb_clear(dlb, u); dlb_clear(dlb, v); dlb_clear(dlb, x); dlb_clear(dlb, y);
 }
 
 // One warp applies move mv: the window's cities before mv.c1 get
 // their bits set, then the shorter of the two paths between the removed edges
 // is reversed and the move's edges and bits are updated.
-__device__ __forceinline__ void apply_move(const TourView &tv, unsigned char *dlb, const Move &mv,
+__device__ __forceinline__ void apply_move(const TourView &tv, uint32_t *dlb, const Move &mv,
                                            int l, int lane)
 {
     const int n = tv.n;
-    for (int c = l + lane; c < mv.c1; c += 32) dlb[c] = 1;
+    dlb_set_range(dlb, l, mv.c1, lane, 32);
     const int p = mv.p, q = mv.q;
     int pa, pb, ca, cb;  // path [pa..pb]; complement [ca..cb]
     if (mv.side == 0) {
@@ -242,7 +261,8 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
     tv.edge = reinterpret_cast<int32_t *>(smem + L.edge);
     tv.tour = reinterpret_cast<int32_t *>(smem + L.tour);
     tv.pos = reinterpret_cast<int32_t *>(smem + L.pos);
-    unsigned char *s_dlb = smem + L.dlb;
+    uint32_t *s_dlb = reinterpret_cast<uint32_t *>(smem + L.dlb);
+    const int dlb_words = (n + 31) >> 5;
     const Geometry<XY, STAGED> g{a, reinterpret_cast<const int2 *>(smem + L.xy),
                                  reinterpret_cast<const uint16_t *>(smem + L.nn)};
     __shared__ int s_first[3];
@@ -296,7 +316,7 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
         bool capped = false;
         uint32_t round = 0;  // selects the key slot
         for (;;) {  // runs
-            for (int i = tid; i < n; i += W) s_dlb[i] = 0;
+            for (int i = tid; i < dlb_words; i += W) s_dlb[i] = 0;
             __syncthreads();
             long long run_moves = 0;
             bool improved = true;
@@ -308,7 +328,7 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                     const int wend = l + w < n ? l + w : n;
                     int mine = INT_MAX;
                     for (int c1 = l + warp; c1 < wend; c1 += NW) {  // warp-uniform
-                        if (s_dlb[c1]) continue;
+                        if (dlb_get(s_dlb, c1)) continue;
                         Move mv;
                         if (find_move_warp<XY, STAGED>(a, g, tv, c1, lane, mv)) {
                             if (lane == 0) s_move[warp] = mv;
@@ -323,7 +343,7 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                     if (tid == 0) s_first[(round + 2) % 3] = INT_MAX;  // no one reads it for two rounds
                     ++round;
                     if (first == INT_MAX) {
-                        for (int c = l + tid; c < wend; c += W) s_dlb[c] = 1;
+                        dlb_set_range(s_dlb, l, wend, tid, W);
                         l = wend;
                         w = w * 2 < W ? w * 2 : W;
                         continue;
@@ -391,6 +411,11 @@ cudaError_t launch_one(const TwoOptArgs &a, int grid, int threads, size_t smem, 
 
 size_t two_opt_smem(int n, int k, bool staged) { return Layout::make(n, k, staged).total; }
 
+bool two_opt_fits(int n, int k, bool staged, size_t smem_optin)
+{
+    return two_opt_smem(n, k, staged) + 2048 <= smem_optin;
+}
+
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s)
 {
     if (a.xy)
@@ -405,7 +430,7 @@ cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms
 {
     if (iteration_best) {
         // one tour, one CTA: stage coordinates and lists when they fit
-        const bool staged = a.xy && two_opt_smem(a.n, a.k, true) <= (size_t)smem_optin;
+        const bool staged = a.xy && two_opt_fits(a.n, a.k, true, (size_t)smem_optin);
         const size_t smem = two_opt_smem(a.n, a.k, staged);
         if (staged) return launch_one<true, true, true>(a, 1, 1024, smem, s);
         if (a.xy) return launch_one<true, false, true>(a, 1, 1024, smem, s);

@@ -21,6 +21,9 @@ struct TwoOptArgs {
 // Dynamic shared memory of one 2-opt CTA for an n-city tour with k
 // neighbours; `staged` adds the coordinates and the 16-bit neighbour lists.
 size_t two_opt_smem(int n, int k, bool staged);
+// Whether the dynamic layout plus the kernel's static shared memory (under
+// 2 KB) fits in `smem_optin` bytes.
+bool two_opt_fits(int n, int k, bool staged, size_t smem_optin);
 cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, int smem_optin,
                            cudaStream_t s);
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s);

@@ -31,12 +31,12 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
            "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
-           "mmas_prior_destroy", "mmas_prior_last_error",
+           "mmas_prior_destroy", "mmas_prior_last_error", "mmas_prior_apply_weighted",
            "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
            "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
            "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
            "mmas_batch_enable_phase_timing", "mmas_batch_phase_times", "mmas_batch_fallback_steps",
-           "mmas_batch_destroy", "mmas_batch_last_error"]
+           "mmas_batch_destroy", "mmas_batch_last_error", "mmas_batch_colony"]
 MMAS_NOALLOC_MAX_ANTS = 1048576
 
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH):
             "mmas_prior_train": (C.c_int, [H, H, P(i32), i32, f32, P(f32)]),
             "mmas_prior_grad": (C.c_int, [H, H, P(i32), P(f32), P(f32)]),
             "mmas_prior_apply": (C.c_int, [H, H]),
+            "mmas_prior_apply_weighted": (C.c_int, [H, H, f32]),
             "mmas_prior_destroy": (None, [H]),
             "mmas_prior_last_error": (C.c_char_p, [H]),
             "mmas_batch_create": (C.c_int, [P(mmas_instance), i32, P(mmas_params), P(H)]),
@@ -132,6 +133,7 @@ def load(path: str = LIB_PATH):
             "mmas_batch_fallback_steps": (C.c_int, [H, P(i64)]),
             "mmas_batch_destroy": (None, [H]),
             "mmas_batch_last_error": (C.c_char_p, [H]),
+            "mmas_batch_colony": (C.c_int, [H, i32, P(H)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(L, name)
@@ -320,10 +322,21 @@ class Colony:
         self.ant_offset = int(ant_offset)
         self._h = mmas_create(xy=xy, dist=dist, params=p)
 
+    @classmethod
+    def _borrowed(cls, h, n, m, cl, owner):
+        # a handle owned by `owner` (a Batch): close() only drops the reference
+        self = cls.__new__(cls)
+        self.n, self.m, self.cl, self.ant_offset = n, m, cl, 0
+        self._h = h
+        self._owner = owner
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
-            mmas_destroy(self._h)
+            if getattr(self, "_owner", None) is None:
+                mmas_destroy(self._h)
             self._h = None
+            self._owner = None
 
     __del__ = close
 
@@ -453,6 +466,9 @@ class Prior:
     def apply(self, colony: "Colony"):
         _pcheck(self._p, load().mmas_prior_apply(self._p, colony._h))
 
+    def apply_weighted(self, colony: "Colony", gamma: float = 1.0):
+        _pcheck(self._p, load().mmas_prior_apply_weighted(self._p, colony._h, float(gamma)))
+
 
 # ------------------------------------------------------------------- batches
 
@@ -501,6 +517,7 @@ class Batch:
         p.stream = stream
         self.ns = [np.asarray(x if x is not None else d).shape[0] for x, d in insts]
         self.ms = [int(m) if m else n for n in self.ns]
+        self.cl = cl
         self._b = mmas_batch_create(insts, p)
 
     def close(self):
@@ -527,6 +544,12 @@ class Batch:
         length = C.c_int32()
         _bcheck(self._b, load().mmas_batch_best_tour(self._b, c, _i32p(tour), C.byref(length)))
         return length.value, tour
+
+    def colony(self, c: int) -> "Colony":
+        """Colony c as a Colony object sharing the batch's state (owned by the batch)."""
+        h = C.c_void_p()
+        _bcheck(self._b, load().mmas_batch_colony(self._b, int(c), C.byref(h)))
+        return Colony._borrowed(h, self.ns[c], self.ms[c], self.cl, self)
 
     def best_lengths(self):
         out = np.zeros(len(self.ns), np.int32)

@@ -115,3 +115,30 @@ def test_batch_errors_and_timing():
     assert c > 0 and r > 0 and abs(t - c - r) < 1e-6
     assert all(x > 0 for x in bt.best_lengths())
     bt.close()
+
+
+def test_batch_colony_handle_shares_state():
+    from paper_2003_11902_gb300 import Prior
+    xys = [I.uniform(n, 70 + n) for n in (150, 400, 90)]
+    bt = Batch(xys=xys, m=16, cl=16, seed=3)
+    bt.iterate(2)
+    col = bt.colony(1)
+    blen, btour = bt.best_tour(1)
+    clen, ctour = col.best_tour()
+    assert clen == blen and np.array_equal(ctour, btour)
+    # an iteration on the handle advances the batch's colony 1 (and only it)
+    before = bt.best_lengths()
+    col.iterate(3)
+    after = bt.best_lengths()
+    assert after[1] == col.best_tour()[0] and after[1] <= before[1]
+    assert after[0] == before[0] and after[2] == before[2]
+    pr = Prior(I.prior_params(3))
+    s = pr.scores(col)
+    assert s.shape == (400, 16) and np.isfinite(s).all()
+    pr.close()
+    col.close()  # drops the reference only
+    bt.iterate(1)
+    assert (bt.best_lengths() > 0).all()
+    with pytest.raises(MMASError):
+        bt.colony(3)
+    bt.close()

@@ -419,6 +419,53 @@ def test_two_opt_matches_oracle(kind, n, m, cl, ls, iters):
     g.close()
 
 
+def _exact_d(xy, a, b):
+    """nint of the Euclidean distance in integers (TSPLIB EUC_2D), vectorised."""
+    dx = xy[a, 0].astype(np.int64) - xy[b, 0]
+    dy = xy[a, 1].astype(np.int64) - xy[b, 1]
+    s = dx * dx + dy * dy
+    q = np.floor(np.sqrt(s.astype(np.float64))).astype(np.int64)
+    q -= (q * q > s)
+    q += ((q + 1) * (q + 1) <= s)
+    return q + (s > q * q + q)
+
+
+def test_two_opt_iteration_best_at_n18500_is_a_local_optimum():
+    """The largest size 2-opt takes (n = 18,500, the paper's d18512 shape): the
+    improved iteration best is a permutation of exact length on which no 2-opt
+    move over the 16 nearest neighbours (either side) shortens the tour."""
+    spatial = pytest.importorskip("scipy.spatial")
+    n, k = 18500, 16
+    xy = I.uniform(n, 18500)
+    g = Colony(xy=xy, m=8, cl=k, ls=1, seed=3)
+    g.iterate(1)
+    blen, t = g.best_tour()
+    assert is_permutation(t, n)
+    nxt = np.roll(t, -1)
+    assert blen == int(_exact_d(xy, t, nxt).sum())
+    # the k nearest by (exact distance, id): exact among 40 float-nearest
+    _, near = spatial.cKDTree(xy.astype(np.float64)).query(xy.astype(np.float64), k=41)
+    near = near[:, 1:]
+    dn = _exact_d(xy, np.repeat(np.arange(n), 40), near.ravel()).reshape(n, 40)
+    order = np.lexsort((near, dn), axis=1)[:, :k]
+    nn = np.take_along_axis(near, order, axis=1)
+    assert (np.take_along_axis(dn, order, axis=1)[:, -1] < dn.max(axis=1)).all()
+    pos = np.empty(n, np.int64)
+    pos[t] = np.arange(n)
+    succ = t[(pos + 1) % n]
+    pred = t[(pos - 1) % n]
+    c1 = np.repeat(np.arange(n), k)
+    c2 = nn.ravel()
+    d12 = _exact_d(xy, c1, c2)
+    rs = _exact_d(xy, c1, succ[c1])
+    gain_s = rs + _exact_d(xy, c2, succ[c2]) - d12 - _exact_d(xy, succ[c1], succ[c2])
+    rp = _exact_d(xy, c1, pred[c1])
+    gain_p = rp + _exact_d(xy, c2, pred[c2]) - d12 - _exact_d(xy, pred[c1], pred[c2])
+    assert not ((d12 < rs) & (gain_s > 0)).any(), "an improving successor-side move remains"
+    assert not ((d12 < rp) & (gain_p > 0)).any(), "an improving predecessor-side move remains"
+    g.close()
+
+
 def test_two_opt_needs_candidate_lists():
     with pytest.raises(MMASError, match="ls needs"):
         Colony(xy=I.uniform(30, 1), cl=0, ls=1)

@@ -95,3 +95,30 @@ def test_prior_needs_coordinates_and_16_candidates():
         pr.apply(col)
     col.close()
     pr.close()
+
+
+def test_weighted_apply_scales_the_heuristic():
+    xy = I.uniform(300, 91)
+    col = Colony(xy=xy, m=8, cl=16, seed=2)
+    eb0 = col.setup()["eta_beta"].astype(np.float64)
+    pr = Prior(I.prior_params(4))
+    pr.apply_weighted(col, 0.0)  # gamma = 0: plain MMAS
+    assert np.array_equal(col.setup()["eta_beta"], eb0.astype(np.float32))
+    s = pr.scores(col).astype(np.float64)
+    p = 1 / (1 + np.exp(-s))
+    pr.apply_weighted(col, 2.0)
+    st = col.setup()
+    eb, nn = st["eta_beta"].astype(np.float64), st["cand"][:, :16]
+    rows = np.arange(300)[:, None]
+    np.testing.assert_allclose(eb[rows, nn], eb0[rows, nn] * p ** 2, rtol=1e-5)
+    mask = np.ones_like(eb, bool)
+    mask[rows, nn] = False
+    scale = (p.min(axis=1) ** 2)[:, None] * np.ones_like(eb)
+    np.testing.assert_allclose(eb[mask], (eb0 * scale)[mask], rtol=1e-5)
+    col.iterate(2)
+    tours, _ = col.tours()
+    assert all(sorted(t) == list(range(300)) for t in tours)
+    with pytest.raises(MMASError, match="gamma"):
+        pr.apply_weighted(col, -1.0)
+    pr.close()
+    col.close()
