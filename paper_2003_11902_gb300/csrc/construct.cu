@@ -227,8 +227,25 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
     return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
 }
 
+// Slot `idx` (row cur) of the candidate table: cc / cw are the staged (or
+// global) table; PART: only rows below a.stage_rows are staged and the others
+// are read from the global table.
+template <bool PART>
+__device__ __forceinline__ void cand_load(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                          int cur, int idx, uint32_t &v, float &w)
+{
+    if constexpr (PART) {
+        const bool st = cur < a.stage_rows;
+        v = (st ? cc : a.cand16)[idx];
+        w = (st ? cw : a.cwinv)[idx];
+    } else {
+        v = cc[idx];
+        w = cw[idx];
+    }
+}
+
 // One candidate-list step: lane c scores slot c of cur's list.
-template <int TW>
+template <int TW, bool PART>
 __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t *cc,
                                          const float *cw, const Tabu<TW> &tb, int lane,
                                          int cur, float lg, int t, int ant, uint32_t it,
@@ -237,11 +254,7 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     const bool act = lane < a.cl;
     uint32_t v = 0;
     float wi = 0.0f;
-    if (act) {
-        const int idx = cur * a.cl + lane;
-        v = cc[idx];
-        wi = cw[idx];
-    }
+    if (act) cand_load<PART>(a, cc, cw, cur, cur * a.cl + lane, v, wi);
     const uint32_t word = tb.word_of((int)v);
     const bool ok = act && !((word >> (v & 31)) & 1u);
     const uint32_t k = ok ? ord_key(__fmul_rn(lg, wi)) : 0u;
@@ -263,7 +276,7 @@ __device__ __forceinline__ void store_window(int32_t *trow, int lane, int w, int
 // of group g+1 runs in slices and its log2s replace lg.  CHECK: skip t == 0 and
 // t >= n and store windows here (first and last groups); otherwise the caller
 // stores the window after every eighth group.
-template <bool CHECK, int TW>
+template <bool CHECK, int TW, bool PART>
 __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_t *cc,
                                            const float *cw, Tabu<TW> &tb, int32_t *trow,
                                            int lane, int ant, uint32_t it, int g, float (&lg)[4],
@@ -287,7 +300,7 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
         }
         const int t = 4 * g + j;
         if (CHECK && (t == 0 || t >= a.n)) continue;
-        const int next = cand_step<TW>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
+        const int next = cand_step<TW, PART>(a, cc, cw, tb, lane, cur, lg[j], t, ant, it, fbn);
         tb.mark(lane, next);
         twin = (lane == tb32 + j) ? next : twin;
         if (CHECK && ((t & 31) == 31 || t == a.n - 1)) store_window(trow, lane, t >> 5, t, twin);
@@ -304,7 +317,7 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
 // interleave.  Only a frozen group leaves the block: that step takes the
 // out-of-line fallback and the group's remaining steps run one by one.  The
 // result equals cand_group's step for step.
-template <int TW>
+template <int TW, bool PART>
 __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const uint16_t *cc,
                                                 const float *cw, Tabu<TW> &tb, int lane,
                                                 int ant, uint32_t it, int g, float (&lg)[4],
@@ -330,8 +343,9 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
             nl[3] = log2f(unit_open(nx.w));
         }
         const int idx = act ? cur * a.cl + lane : 0;
-        const uint32_t v = cc[idx];
-        const float wi = cw[idx];
+        uint32_t v;
+        float wi;
+        cand_load<PART>(a, cc, cw, cur, idx, v, wi);
         const uint32_t word = tb.word_of((int)v);
         const bool ok = act && !((word >> (v & 31)) & 1u);
         const uint32_t k = ok ? ord_key(__fmul_rn(lg[j], wi)) : 0u;
@@ -356,8 +370,8 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
 #pragma unroll
         for (int j = 1; j < 4; ++j) {
             if (j <= jfail) continue;
-            const int next = cand_step<TW>(a, cc, cw, tb, lane, cur, lg[j], 4 * g + j, ant,
-                                                it, fbn);
+            const int next = cand_step<TW, PART>(a, cc, cw, tb, lane, cur, lg[j], 4 * g + j, ant,
+                                                 it, fbn);
             tb.mark(lane, next);
             twin = (lane == tb32 + j) ? next : twin;
             cur = next;
@@ -371,7 +385,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
 // trow: a uniform start (Alg. 1), then n - 1 selections.  `it` is the
 // iteration index; cc / cw are the candidate table (staged or global) or the
 // reciprocal weight matrix (whole-row mode).
-template <int MODE, int TW>
+template <int MODE, int TW, bool PART = false>
 __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_t *cc,
                                            const float *cw, Tabu<TW> &tb, int lane, int ant,
                                            uint32_t it, int32_t *trow)
@@ -396,14 +410,14 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
             lg[2] = log2f(unit_open(r.z));
             lg[3] = log2f(unit_open(r.w));
         }
-        cand_group<true, TW>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
+        cand_group<true, TW, PART>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
         int g = 1;
         for (; 4 * g + 3 <= a.n - 1; ++g) {
-            cand_group_spec<TW>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
+            cand_group_spec<TW, PART>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
             if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
         }
         if (4 * g <= a.n - 1)
-            cand_group<true, TW>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
+            cand_group<true, TW, PART>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
         else if (g > 1 && ((g - 1) & 7) != 7)
             store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
     } else {
@@ -449,7 +463,9 @@ __device__ __forceinline__ bool stage_table(unsigned char *s_w, const void *src_
     return true;
 }
 
-template <int MODE, bool STAGED, int TW>
+// STAGED: 0 the table is read from global memory; 1 it is staged whole; 2
+// its first a.stage_rows rows are staged (candidate-list mode).
+template <int MODE, int STAGED, int TW>
 __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -459,7 +475,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     const float *cw = (MODE == CAND) ? a.cwinv : a.wmat;
     const uint16_t *cc = a.cand16;
     size_t off = 0;
-    if constexpr (STAGED) {
+    if constexpr (STAGED != 0) {
         unsigned char *s_w = smem;
         off = a.stage_w_bytes;
         unsigned char *s_c = smem + off;
@@ -486,7 +502,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     const int ant_end = a.ant_offset + a.m;
     int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
     for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride)
-        build_tour<MODE, TW>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
+        build_tour<MODE, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
 }
 
 // Batched construction (NEXT-2): one persistent launch builds every ant of
@@ -495,7 +511,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
 // decreasing n so the longest tours start first -- loads that colony's
 // arguments, stages its candidate table when table and tabus fit in
 // `smem_bytes`, and builds the chunk's tours.  Candidate-list mode only.
-template <int TW, bool STAGED>
+template <int TW, int STAGED>
 __device__ __forceinline__ void batch_chunk(const ConstructArgs &a, unsigned char *smem,
                                             uint64_t *bar, uint32_t &parity, int first, int count,
                                             int lane, int warp)
@@ -504,7 +520,7 @@ __device__ __forceinline__ void batch_chunk(const ConstructArgs &a, unsigned cha
     const uint16_t *cc = a.cand16;
     const float *cw = a.cwinv;
     size_t off = 0;
-    if constexpr (STAGED) {
+    if constexpr (STAGED != 0) {
         const bool ok = stage_table(smem, a.cwinv, a.stage_w_bytes, smem + a.stage_w_bytes, a.cand16,
                                     a.stage_c_bytes, bar, parity, &a.sc->err);
         parity ^= 1u;
@@ -518,7 +534,7 @@ __device__ __forceinline__ void batch_chunk(const ConstructArgs &a, unsigned cha
     tb.nw = (a.n + 31) >> 5;
     if constexpr (TW == 0) tb.w = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * tb.nw;
     const int ant = first + warp;  // this colony's ant index (ant_offset = 0)
-    build_tour<CAND, TW>(a, cc, cw, tb, lane, ant, it, a.tours + (size_t)ant * a.ld);
+    build_tour<CAND, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, a.tours + (size_t)ant * a.ld);
 }
 
 __global__ void __launch_bounds__(384, 1)
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(384, 1)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(16) ConstructArgs s_a;
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ int s_chunk;
+    __shared__ int s_chunk, s_mode;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t parity = 0;
     if (threadIdx.x == 0) mbar_init(&s_bar, 1);
@@ -546,16 +562,37 @@ __global__ void __launch_bounds__(384, 1)
                 dst[i] = src[i];
         }
         __syncthreads();
+        // stage the whole table when it fits with the tabus, else its first
+        // rows (a multiple of 8, at least 64), else none
+        if (threadIdx.x == 0) {
+            const int tw0 = tabu_words(s_a.n);
+            const size_t masks = tw0 ? 0 : (size_t)nwarps * ((s_a.n + 31) >> 5) * sizeof(uint32_t);
+            if ((size_t)s_a.stage_w_bytes + s_a.stage_c_bytes + masks <= smem_bytes) {
+                s_mode = 1;
+                s_a.stage_rows = s_a.n;
+            } else {
+                const size_t avail = smem_bytes > masks ? smem_bytes - masks : 0;
+                const int rows = (int)(avail / ((size_t)s_a.cl * 6)) & ~7;
+                s_mode = rows >= 64 && rows < s_a.n ? 2 : 0;
+                if (s_mode == 2) {
+                    s_a.stage_rows = rows;
+                    s_a.stage_w_bytes = (uint32_t)rows * s_a.cl * 4;
+                    s_a.stage_c_bytes = (uint32_t)rows * s_a.cl * 2;
+                }
+            }
+        }
+        __syncthreads();
         const ConstructArgs &a = s_a;
         const int tw = tabu_words(a.n);
-        const size_t masks = tw ? 0 : (size_t)nwarps * ((a.n + 31) >> 5) * sizeof(uint32_t);
-        const bool staged = (size_t)a.stage_w_bytes + a.stage_c_bytes + masks <= smem_bytes;
+        const int mode = s_mode;
 #define MMAS_BATCH_CHUNK(TWV)                                                                   \
     do {                                                                                        \
-        if (staged)                                                                             \
-            batch_chunk<TWV, true>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);    \
+        if (mode == 1)                                                                          \
+            batch_chunk<TWV, 1>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);       \
+        else if (mode == 2)                                                                     \
+            batch_chunk<TWV, 2>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);       \
         else                                                                                    \
-            batch_chunk<TWV, false>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);   \
+            batch_chunk<TWV, 0>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);       \
     } while (0)
         if (tw == 1) MMAS_BATCH_CHUNK(1);
         else if (tw == 2) MMAS_BATCH_CHUNK(2);
@@ -788,18 +825,20 @@ __global__ void __launch_bounds__(384, 1) k_construct_var(const ConstructArgs a,
 using KernelFn = void (*)(const ConstructArgs, int);
 
 // tw: tabu words per lane (1, 2, 4), or 0 for the shared-memory tabu
+// staged: 0 none, 1 the whole table, 2 its first rows (candidate lists only)
 KernelFn pick_kernel(int mode, int staged, int tw)
 {
-    static const KernelFn table[16] = {
-        k_construct<CAND, false, 0>, k_construct<CAND, false, 1>, k_construct<CAND, false, 2>,
-        k_construct<CAND, false, 4>, k_construct<CAND, true, 0>,  k_construct<CAND, true, 1>,
-        k_construct<CAND, true, 2>,  k_construct<CAND, true, 4>,  k_construct<ROW, false, 0>,
-        k_construct<ROW, false, 1>,  k_construct<ROW, false, 2>,  k_construct<ROW, false, 4>,
-        k_construct<ROW, true, 0>,   k_construct<ROW, true, 1>,   k_construct<ROW, true, 2>,
-        k_construct<ROW, true, 4>,
+    static const KernelFn cand[3][4] = {
+        {k_construct<CAND, 0, 0>, k_construct<CAND, 0, 1>, k_construct<CAND, 0, 2>, k_construct<CAND, 0, 4>},
+        {k_construct<CAND, 1, 0>, k_construct<CAND, 1, 1>, k_construct<CAND, 1, 2>, k_construct<CAND, 1, 4>},
+        {k_construct<CAND, 2, 0>, k_construct<CAND, 2, 1>, k_construct<CAND, 2, 2>, k_construct<CAND, 2, 4>},
+    };
+    static const KernelFn rowk[2][4] = {
+        {k_construct<ROW, 0, 0>, k_construct<ROW, 0, 1>, k_construct<ROW, 0, 2>, k_construct<ROW, 0, 4>},
+        {k_construct<ROW, 1, 0>, k_construct<ROW, 1, 1>, k_construct<ROW, 1, 2>, k_construct<ROW, 1, 4>},
     };
     const int ti = tw == 4 ? 3 : tw;  // 0, 1, 2, 4 -> 0, 1, 2, 3
-    return table[(mode << 3) | (staged << 2) | ti];
+    return mode == CAND ? cand[staged][ti] : rowk[staged ? 1 : 0][ti];
 }
 
 // whole-row variants: (sel, ct) != (0, 0); TW 1 (n <= 1024) or 0 for the bitmask
@@ -834,6 +873,11 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     w = w < 1 ? 1 : (w > 12 ? 12 : w);
     const size_t masks = (size_t)w * per_warp;
     const size_t need = table + 16 + masks;
+    // candidate lists too large to stage whole: stage their first rows (a
+    // multiple of 8), the rest is read from global memory
+    const size_t avail = smem_optin > 16 + masks ? smem_optin - 16 - masks : 0;
+    const int part_rows = row ? 0 : (int)(avail / ((size_t)a.cl * 6)) & ~7;
+    plan->stage_rows = a.n;
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
         plan->cons_warps = w;
@@ -841,6 +885,14 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         const int g = (a.m + w - 1) / w;
         plan->grid = g < num_sms ? g : num_sms;
         plan->smem = need;
+    } else if (!var && part_rows >= 64 && part_rows < a.n) {
+        plan->staged = 2;
+        plan->stage_rows = part_rows;
+        plan->cons_warps = w;
+        plan->gen_warps = 0;
+        const int g = (a.m + w - 1) / w;
+        plan->grid = g < num_sms ? g : num_sms;
+        plan->smem = (size_t)part_rows * a.cl * 6 + 16 + masks;
     } else {
         plan->staged = 0;
         plan->cons_warps = 4;
@@ -872,9 +924,13 @@ cudaError_t launch_construct_batch(const ConstructArgs *args, const BatchChunk *
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s)
 {
     ConstructArgs b = a;
+    b.stage_rows = plan.stage_rows;
     if (!plan.staged) {
         b.stage_w_bytes = 0;
         b.stage_c_bytes = 0;
+    } else if (plan.staged == 2) {
+        b.stage_w_bytes = (uint32_t)plan.stage_rows * a.cl * 4;
+        b.stage_c_bytes = (uint32_t)plan.stage_rows * a.cl * 2;
     } else if (a.cl == 0) {
         b.stage_w_bytes = (uint32_t)((size_t)a.n * a.ld * sizeof(float));
         b.stage_c_bytes = 0;

@@ -195,6 +195,7 @@ struct ConstructArgs {
     Scalars *sc;
     uint32_t stage_w_bytes;    // bytes of the staged weight table (16-byte multiple)
     uint32_t stage_c_bytes;    // bytes of the staged id table (16-byte multiple)
+    int32_t stage_rows;        // rows of the candidate table staged (n when whole)
     int32_t sel;               // whole-row selection: 0 reservoir sampling, 1 roulette wheel
     int32_t ct;                // whole-row tabu: 0 bitmask, 1 compact list
     // greedy-fallback reach list (candidate-list mode, fallback 0; xe = 0: none,
@@ -216,7 +217,8 @@ struct BatchChunk {
 };
 
 struct ConstructPlan {
-    int staged;     // stage the weight (and id) tables in shared memory
+    int staged;     // 0: no staging; 1: the whole table in shared memory; 2: its first stage_rows rows
+    int stage_rows;
     int tw;         // tabu words per lane in registers (1, 2, 4; n <= 1024 tw), 0: shared memory
     int cons_warps; // warps building tours (one ant each) per CTA
     int gen_warps;  // reserved (0)
