@@ -102,6 +102,20 @@ struct Geometry {
         else
             return __ldg(a.nn + (size_t)c * a.k + h);
     }
+    // squared Euclidean distance (coordinate instances)
+    __device__ __forceinline__ long long sq(int u, int v) const
+    {
+        int2 pu, pv;
+        if constexpr (STAGED) {
+            pu = sxy[u];
+            pv = sxy[v];
+        } else {
+            pu = __ldg(a.xy + u);
+            pv = __ldg(a.xy + v);
+        }
+        const long long dx = (long long)pu.x - pv.x, dy = (long long)pu.y - pv.y;
+        return dx * dx + dy * dy;
+    }
     // d(c, c2) for c2, neighbour h of c
     __device__ __forceinline__ int neighbour_dist(int c, int h, int c2) const
     {
@@ -120,6 +134,13 @@ struct Move {
     int32_t c1, side, p, q, d12, d34;
 };
 
+// nint(sqrt(s)) < t, exactly, from the squared distance s: for t >= 1 it holds
+// iff sqrt(s) < t - 1/2 (sqrt(s) is never a half-integer), that is s <= t^2 - t.
+__device__ __forceinline__ bool nint_sqrt_below(long long s, long long t)
+{
+    return t > 0 && s <= t * t - t;
+}
+
 // First improving move at city c1, searched by one warp: lane h examines
 // neighbour h (h < k <= 32) on both sides.  The sequential scan of a side stops
 // at the first neighbour not closer than the tour neighbour on that side; the
@@ -136,26 +157,41 @@ __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geomet
     const int s1 = tv.tour[pn], p1 = tv.tour[pp];
     const int rs = tv.edge[p], rp = tv.edge[pp];
     bool vs = false, vp = false;
-    int q = 0, d12 = 0, dss = 0, dpp = 0;
+    int q = 0, d12 = 0, tn = 0, tp = 0, dss = 0, dpp = 0;
     if (lane < a.k) {
         const int c2 = g.neighbour(c1, lane);
         d12 = g.neighbour_dist(c1, lane, c2);
         q = tv.pos[c2];
         const int qn = tv.nxt(q), qp = tv.prv(q);
-        dss = g.d(s1, tv.tour[qn]);
-        dpp = g.d(p1, tv.tour[qp]);
-        vs = d12 < rs && (long long)rs + tv.edge[q] - d12 - dss > 0;
-        vp = d12 < rp && (long long)rp + tv.edge[qp] - d12 - dpp > 0;
+        tn = tv.tour[qn];
+        tp = tv.tour[qp];
+        // improving: d(s1, succ c2) < rs + d(c2, succ c2) - d12, and alike on
+        // the predecessor side; with coordinates the test runs on the squared
+        // distance, without a square root
+        const long long ts = (long long)rs + tv.edge[q] - d12, tq = (long long)rp + tv.edge[qp] - d12;
+        if constexpr (XY) {
+            vs = d12 < rs && nint_sqrt_below(g.sq(s1, tn), ts);
+            vp = d12 < rp && nint_sqrt_below(g.sq(p1, tp), tq);
+        } else {
+            dss = g.d(s1, tn);
+            dpp = g.d(p1, tp);
+            vs = d12 < rs && dss < ts;
+            vp = d12 < rp && dpp < tq;
+        }
     }
     const unsigned ms = __ballot_sync(0xFFFFFFFFu, vs), mp = __ballot_sync(0xFFFFFFFFu, vp);
     if ((ms | mp) == 0u) return false;
     const int h = __ffs(ms ? ms : mp) - 1;
+    int d34 = ms ? dss : dpp;
+    if constexpr (XY) {
+        if (lane == h) d34 = ms ? g.d(s1, tn) : g.d(p1, tp);  // the added edge, exactly
+    }
     mv.c1 = c1;
     mv.side = ms ? 0 : 1;
     mv.p = p;
     mv.q = __shfl_sync(0xFFFFFFFFu, q, h);
     mv.d12 = __shfl_sync(0xFFFFFFFFu, d12, h);
-    mv.d34 = __shfl_sync(0xFFFFFFFFu, ms ? dss : dpp, h);
+    mv.d34 = __shfl_sync(0xFFFFFFFFu, d34, h);
     return true;
 }
 
