@@ -446,6 +446,22 @@ def run_ours(args, w):
             "paper_context": "V100, pr1002, cl=32, MMAS-WRS-BT: 0.93 ms construction "
                              "(~1.08M tours/s), Table 6",
         }
+        if w["cl"] > 0:
+            # the same kernel against the arithmetic ceiling of its steps: every
+            # candidate slot draws at every step (Philox word, log2, key), measured
+            # at full occupancy by the library's probe in this run
+            from paper_2003_11902_gb300 import mmas as _mm
+            draws = w["m"] * (w["n"] - 1) * w["cl"]
+            rate = _mm.mmas_probe_draw_rate(dev, 50.0) / 1e9
+            sched = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+            got = draws / (c_ms * 1e-3) / 1e9
+            line["roofline_alu"] = {
+                "kernel": "k_construct", "bound": "alu", "achieved": got, "peak": rate,
+                "unit": "Gdraws/s", "frac": got / rate, "algorithmic_draws_per_launch": draws,
+                "peak_kind": "measured (mmas_probe_draw_rate: Philox + log2 + key per draw at full "
+                             "occupancy, same run)",
+                "binding": f"neither: the step-to-step dependency chain of each ant (about 300 "
+                           f"cycles a step) with {w['m']} ants on {sched} warp schedulers"}
         gapres = None if args.no_gap else time_to_gap(w, xy, seed, dev, stream.cuda_stream)
         if gapres is not None:
             line["time_to_2pct_gap"] = gapres
@@ -620,12 +636,40 @@ def run_ours_batch(args, w):
             "best_len_mean": float(np.mean(best)), "fallback_steps": int(fb),
             "wall_s": wall,
         }
+        if ws == 1:
+            line["vs_single_colonies"] = _single_colonies(w, xys, seed, dev, stream.cuda_stream,
+                                                          args.warmup + args.steps, args.steps,
+                                                          total_ms, best)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_batch(w, xys)
         print(json.dumps(line), flush=True)
     bt.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _single_colonies(w, xys, seed, dev, stream, iters, timed, batch_ms, batch_best):
+    """The batch's colonies run one at a time as ordinary colonies (colony b with
+    seed + b), for the same iterations: device time of the last `timed`
+    iterations of each, summed, against the batch's; and whether every colony
+    reaches the same best length (the batch equals its colonies run alone)."""
+    from paper_2003_11902_gb300 import Colony
+
+    ms, same = 0.0, True
+    for b, xy in enumerate(xys):
+        col = Colony(xy=xy, m=len(xy), cl=w["cl"], seed=seed + b, device=dev, stream=stream, **PARAMS)
+        col.iterate(iters - timed)
+        col.enable_phase_timing(True)
+        for _ in range(timed):
+            col.iterate(1)
+            ms += col.phase_times()[2]
+        same = same and col.best_tour()[0] == int(batch_best[b])
+        col.close()
+    return {"colonies": len(xys), "iterations_each": iters, "timed_iterations": timed,
+            "single_ms_per_iteration_of_all": ms / timed, "batched_ms_per_iteration": batch_ms / timed,
+            "speedup": ms / batch_ms, "same_best_lengths": bool(same),
+            "note": "device time (CUDA events in each colony's iteration graph); the batch and the "
+                    "colonies run alone build the same tours, so any time-to-quality ratio is this one"}
 
 
 def _race(col, seconds, target, check_every=5):
