@@ -330,9 +330,11 @@ const char *mmas_prior_last_error(const mmas_prior *p);
  * names the colony), ENOMEM, ECUDA; on error nothing is created. */
 typedef struct mmas_batch mmas_batch;
 
-/* Launch shape of the batched construction: warps (= ants) per CTA, 1..12,
- * and CTAs per SM, 1..4 (shared memory per CTA is the SM's share).  Results do
- * not depend on it. */
+/* Launch shape of the batched construction: warps (= ants) per CTA and CTAs
+ * per SM, 1..4 (shared memory per CTA is the SM's share); warps per CTA times
+ * CTAs per SM is at most 16 when every colony has n <= 2048, else at most 12
+ * (the registers of an SM).  The default is 16 (or 12) warps, one CTA per SM.
+ * Results do not depend on it. */
 typedef struct {
     int32_t warps_per_cta;
     int32_t ctas_per_sm;

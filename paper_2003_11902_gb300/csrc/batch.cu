@@ -161,6 +161,11 @@ mmas_status gather(mmas_batch *b)
     return MMAS_OK;
 }
 
+// Every colony has n <= 2048: the batched construction's narrow variant, whose
+// register budget lets 16 warps share an SM (12 otherwise).
+bool narrow(const mmas_batch *b) { return b->max_n <= 2048; }
+int max_warps(const mmas_batch *b) { return narrow(b) ? 16 : 12; }
+
 // Shared memory per construction CTA for `ctas` CTAs per SM.
 size_t cta_smem_for(const mmas_batch *b, int ctas)
 {
@@ -173,10 +178,14 @@ size_t cta_smem_for(const mmas_batch *b, int ctas)
 
 mmas_status check_config(mmas_batch *b, const mmas_batch_config &c, size_t *smem)
 {
-    if (c.warps_per_cta < 1 || c.warps_per_cta > 12 || c.ctas_per_sm < 1 || c.ctas_per_sm > 4)
-        return bfail(b, MMAS_EINVAL, "warps_per_cta must be in 1..12 and ctas_per_sm in 1..4");
-    if (c.warps_per_cta * c.ctas_per_sm > 12)
-        return bfail(b, MMAS_EINVAL, "at most 12 construction warps fit one SM's registers");
+    const int wmax = max_warps(b);
+    if (c.warps_per_cta < 1 || c.warps_per_cta > wmax || c.ctas_per_sm < 1 || c.ctas_per_sm > 4)
+        return bfail(b, MMAS_EINVAL, wmax == 16 ? "warps_per_cta must be in 1..16 and ctas_per_sm in 1..4"
+                                                : "warps_per_cta must be in 1..12 (a colony has n > 2048) "
+                                                  "and ctas_per_sm in 1..4");
+    if (c.warps_per_cta * c.ctas_per_sm > wmax)
+        return bfail(b, MMAS_EINVAL, "warps_per_cta x ctas_per_sm exceeds the construction warps one "
+                                     "SM's registers hold (16, or 12 with a colony of n > 2048)");
     const size_t s = cta_smem_for(b, c.ctas_per_sm);
     // the shared-memory tabus of the largest colony must fit when its table does not
     const size_t masks =
@@ -214,7 +223,8 @@ mmas_status enqueue_construct(mmas_batch *b, cudaStream_t s)
 {
     BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s));
     BCK(b, launch_construct_batch(b->d_cargs, b->d_chunks, b->nchunks, b->d_counter,
-                                  b->num_sms * b->cfg.ctas_per_sm, b->cfg.warps_per_cta, b->cta_smem, s));
+                                  b->num_sms * b->cfg.ctas_per_sm, b->cfg.warps_per_cta, b->cta_smem,
+                                  narrow(b), s));
     return MMAS_OK;
 }
 
@@ -268,7 +278,7 @@ mmas_status apply_config(mmas_batch *b, const mmas_batch_config &c)
     if (st != MMAS_OK) return st;
     st = build_chunks(b, c.warps_per_cta);
     if (st != MMAS_OK) return st;
-    BCK(b, prepare_construct_batch(smem));
+    BCK(b, prepare_construct_batch(smem, narrow(b)));
     b->cfg = c;
     b->cta_smem = smem;
     return MMAS_OK;
@@ -342,7 +352,7 @@ mmas_status create_batch(mmas_batch *b, const mmas_instance *insts, int count, c
     BCK(b, cudaMallocHost(&b->h_best, (size_t)B * sizeof(int32_t)));
     BCK(b, cudaMallocHost(&b->h_gather, 2 * sizeof(unsigned long long)));
     BCK(b, cudaStreamSynchronize(b->stream));
-    mmas_batch_config c0{12, 1};
+    mmas_batch_config c0{max_warps(b), 1};
     if ((st = apply_config(b, c0)) != MMAS_OK) return st;
     if ((st = capture(b)) != MMAS_OK) return st;
     return gather(b);
@@ -482,7 +492,11 @@ mmas_status mmas_batch_autotune(mmas_batch *b, int32_t reps, mmas_batch_config *
     if (reps < 1) return bfail(b, MMAS_EINVAL, "reps must be >= 1");
     DeviceGuard g(b->device);
     BCK(b, cudaStreamSynchronize(b->stream));
-    static const mmas_batch_config cands[] = {{12, 1}, {8, 1}, {6, 2}, {4, 3}, {3, 4}, {10, 1}};
+    static const mmas_batch_config wide[] = {{12, 1}, {8, 1}, {6, 2}, {4, 3}, {3, 4}, {10, 1}};
+    static const mmas_batch_config narrow_cands[] = {{16, 1}, {14, 1}, {12, 1}, {8, 2}, {4, 4}, {5, 3}};
+    const std::vector<mmas_batch_config> cands =
+        narrow(b) ? std::vector<mmas_batch_config>(std::begin(narrow_cands), std::end(narrow_cands))
+                  : std::vector<mmas_batch_config>(std::begin(wide), std::end(wide));
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));

@@ -537,7 +537,10 @@ __device__ __forceinline__ void batch_chunk(const ConstructArgs &a, unsigned cha
     build_tour<CAND, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, a.tours + (size_t)ant * a.ld);
 }
 
-__global__ void __launch_bounds__(384, 1)
+// NARROW: every colony has n <= 2048 (register tabus of 1 or 2 words), which
+// lets 16 warps of the tighter code share an SM's registers instead of 12.
+template <bool NARROW>
+__global__ void __launch_bounds__(NARROW ? 512 : 384, 1)
     k_construct_batch(const ConstructArgs *__restrict__ args, const BatchChunk *__restrict__ chunks,
                       int nchunks, unsigned *counter, uint32_t smem_bytes)
 {
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(384, 1)
             batch_chunk<TWV, 0>(a, smem, &s_bar, parity, ch.first, ch.count, lane, warp);       \
     } while (0)
         if (tw == 1) MMAS_BATCH_CHUNK(1);
-        else if (tw == 2) MMAS_BATCH_CHUNK(2);
+        else if (NARROW || tw == 2) MMAS_BATCH_CHUNK(2);
         else if (tw == 4) MMAS_BATCH_CHUNK(4);
         else MMAS_BATCH_CHUNK(0);
 #undef MMAS_BATCH_CHUNK
@@ -906,18 +909,23 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
 }
 
-cudaError_t prepare_construct_batch(size_t smem_bytes)
+cudaError_t prepare_construct_batch(size_t smem_bytes, bool narrow)
 {
-    return cudaFuncSetAttribute(reinterpret_cast<const void *>(k_construct_batch),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    const void *k = narrow ? reinterpret_cast<const void *>(k_construct_batch<true>)
+                           : reinterpret_cast<const void *>(k_construct_batch<false>);
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 cudaError_t launch_construct_batch(const ConstructArgs *args, const BatchChunk *chunks, int nchunks,
                                    unsigned *counter, int grid, int warps, size_t smem_bytes,
-                                   cudaStream_t s)
+                                   bool narrow, cudaStream_t s)
 {
-    k_construct_batch<<<grid, warps * 32, smem_bytes, s>>>(args, chunks, nchunks, counter,
-                                                           (uint32_t)smem_bytes);
+    if (narrow)
+        k_construct_batch<true><<<grid, warps * 32, smem_bytes, s>>>(args, chunks, nchunks, counter,
+                                                                     (uint32_t)smem_bytes);
+    else
+        k_construct_batch<false><<<grid, warps * 32, smem_bytes, s>>>(args, chunks, nchunks, counter,
+                                                                      (uint32_t)smem_bytes);
     return cudaGetLastError();
 }
 

@@ -286,10 +286,11 @@ cudaError_t launch_init_colony(int32_t n, int32_t ld, double rho, double p_root,
 cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
                            ConstructPlan *plan);
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s);
-cudaError_t prepare_construct_batch(size_t smem_bytes);
+// narrow: every colony has n <= 2048 (up to 16 warps per SM, else 12)
+cudaError_t prepare_construct_batch(size_t smem_bytes, bool narrow);
 cudaError_t launch_construct_batch(const ConstructArgs *args, const BatchChunk *chunks, int nchunks,
                                    unsigned *counter, int grid, int warps, size_t smem_bytes,
-                                   cudaStream_t s);
+                                   bool narrow, cudaStream_t s);
 
 cudaError_t launch_best(const BestArgs &a, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs &a, int num_sms, cudaStream_t s);

@@ -48,14 +48,21 @@ def test_batch_colonies_match_the_oracle():
     bt.close()
 
 
-def test_launch_shape_does_not_change_results():
-    xys = [I.uniform(n, 700 + n) for n in (200, 1300, 64, 900)]
+@pytest.mark.parametrize("sizes,cfgs,cands", [
+    # every colony n <= 2048: the 16-warp variant of the batched construction
+    ((200, 1300, 64, 900), [(16, 1), (12, 1), (4, 3), (5, 2)],
+     [(16, 1), (14, 1), (12, 1), (8, 2), (4, 4), (5, 3)]),
+    # a colony above 2048 (four-word tabus): the 12-warp variant
+    ((200, 2500, 64), [(12, 1), (4, 3)], [(12, 1), (8, 1), (6, 2), (4, 3), (3, 4), (10, 1)]),
+])
+def test_launch_shape_does_not_change_results(sizes, cfgs, cands):
+    xys = [I.uniform(n, 700 + n) for n in sizes]
     runs = []
-    for cfg in [(12, 1), (4, 3), (5, 2), None]:
+    for cfg in cfgs + [None]:
         bt = Batch(xys=xys, m=40, cl=16, rho=0.05, seed=3)
         if cfg is None:
             chosen = bt.autotune(reps=1)
-            assert chosen in [(12, 1), (8, 1), (6, 2), (4, 3), (3, 4), (10, 1)]
+            assert chosen in cands
             assert bt.fallback_steps() == 0  # autotuning leaves no trace in the counters
         else:
             bt.set_config(*cfg)
@@ -107,8 +114,10 @@ def test_batch_errors_and_timing():
     assert load().mmas_batch_get_tours(bt._b, 2, None, None) == MMAS_EINVAL
     assert "out of range" in load().mmas_batch_last_error(bt._b).decode()
     with pytest.raises(MMASError, match="warps_per_cta"):
-        bt.set_config(13, 1)
-    assert bt.config() == (12, 1)  # a rejected shape leaves the batch as it was
+        bt.set_config(17, 1)
+    with pytest.raises(MMASError, match="exceeds"):
+        bt.set_config(9, 2)
+    assert bt.config() == (16, 1)  # a rejected shape leaves the batch as it was
     bt.enable_phase_timing(True)
     bt.iterate(2)
     c, r, t = bt.phase_times()
