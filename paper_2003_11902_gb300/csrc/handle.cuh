@@ -34,6 +34,7 @@ struct mmas_handle {
     uint2 *xlw = nullptr;            // [n][xe]
     float *xlb = nullptr;            // [n]
     mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
+    int32_t *h_tour = nullptr;      // pinned staging of the best tour
 
     mmas::ConstructArgs cargs{};
     mmas::ConstructPlan cplan{};

@@ -72,6 +72,7 @@ void free_all(mmas_handle *h)
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
+    if (h->h_tour) cudaFreeHost(h->h_tour);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -86,10 +87,14 @@ cudaError_t dalloc(T **p, size_t bytes, cudaStream_t stream)
     return e;
 }
 
-// Read back the scalar block and turn device-raised error bits into a status.
-mmas_status sync_and_check(mmas_handle *h)
+// Read back the scalar block (with `tour` set, also the best tour into the
+// pinned staging buffer, in the same synchronisation) and turn device-raised
+// error bits into a status.
+mmas_status sync_and_check(mmas_handle *h, bool tour = false)
 {
     CK(h, cudaMemcpyAsync(h->h_sc, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+    if (tour)
+        CK(h, cudaMemcpyAsync(h->h_tour, h->gb_tour, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     const uint32_t e = h->h_sc->err;
     if (e) {
@@ -240,6 +245,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     CK(h, dalloc(&h->ext_tour, (size_t)n * sizeof(int32_t), h->stream));
     CK(h, dalloc(&h->ext_len, sizeof(int32_t), h->stream));
     CK(h, cudaMallocHost(reinterpret_cast<void **>(&h->h_sc), sizeof(Scalars)));
+    CK(h, cudaMallocHost(reinterpret_cast<void **>(&h->h_tour), (size_t)n * sizeof(int32_t)));
     std::memset(h->h_sc, 0, sizeof(Scalars));
 
     // instance -> device, distances, overflow check
@@ -434,10 +440,10 @@ mmas_status mmas_best_tour(mmas_handle *h, int32_t *tour_out, int32_t *len_out)
 {
     if (check_handle(h)) return MMAS_EINVAL;
     DeviceGuard g(h->device);
-    mmas_status st = sync_and_check(h);
+    mmas_status st = sync_and_check(h, tour_out != nullptr);
     if (st != MMAS_OK) return st;
     if (h->h_sc->gb_len == INT_MAX) return fail(h, MMAS_ESTATE, "no iteration has completed yet");
-    if (tour_out) CK(h, cudaMemcpy(tour_out, h->gb_tour, (size_t)h->n * 4, cudaMemcpyDeviceToHost));
+    if (tour_out) std::memcpy(tour_out, h->h_tour, (size_t)h->n * 4);
     if (len_out) *len_out = h->h_sc->gb_len;
     return MMAS_OK;
 }
