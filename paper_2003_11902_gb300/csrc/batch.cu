@@ -322,6 +322,9 @@ mmas_status create_batch(mmas_batch *b, const mmas_instance *insts, int count, c
         sa[c] = h->sargs;
         sa[c].best = 1;
         ua[c] = h->uargs;
+        // no extra list for the greedy fallback in batched runs: its upkeep
+        // costs the pass more than the short runs of many colonies gain
+        ua[c].xhot = nullptr;
         scs[c] = h->sc;
         ant_base[c] = (int32_t)ant_colony.size();
         for (int k = 0; k < h->m; ++k) ant_colony.push_back(c);

@@ -169,34 +169,44 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, co
 }
 
 // The greedy fallback decided on cur's reach list: its REACH_MAX nearest nodes
-// (fewer when n is small) with this iteration's choice_info, and `bound`, the
-// largest choice_info of any node outside the list.  When the best unvisited
-// listed node beats the bound strictly, every node of the row's largest
-// choice_info is listed, so the listed winner (ties -> lower id) is the row's
-// greedy choice; otherwise -1 and the caller scans the row.  One memory round
-// trip: lane l holds entries l, l + 32, l + 64, l + 96.
+// (fewer when n is small) and up to REACH_EXTRA other nodes whose trail is
+// above tau_min, with this iteration's choice_info, and `bound`, the largest
+// choice_info of any other node.  When the best unvisited node of the lists
+// beats the bound strictly, every node of the row's largest choice_info is
+// listed, so the listed winner (ties -> lower id) is the row's greedy choice;
+// otherwise -1 and the caller scans the row.  One memory round trip: lane l
+// holds entries l, l + 32, l + 64, l + 96 of the reach list and entry l of
+// the extra list.
+template <int TW>
+__device__ __forceinline__ void reach_entry(uint2 e, bool in, const Tabu<TW> &tb, uint32_t &bk, uint32_t &bv)
+{
+    const uint32_t v = e.y;
+    const uint32_t word = tb.word_of((int)v);  // every lane calls it
+    const bool ok = in && !((word >> (v & 31)) & 1u);
+    const uint32_t k = ok ? (e.x | 0x80000000u) : 0u;  // ord_key of choice_info >= 0
+    if (k > bk || (k == bk && k != 0u && v < bv)) {
+        bk = k;
+        bv = v;
+    }
+}
+
 template <int TW>
 __device__ __forceinline__ int greedy_reach(const uint2 *__restrict__ xl, const float *__restrict__ xb,
-                                            int xe, const Tabu<TW> &tb, int lane)
+                                            int xe, const uint2 *__restrict__ xx, const int32_t *xn,
+                                            const Tabu<TW> &tb, int lane)
 {
     constexpr int P = REACH_MAX / 32;
     uint2 e[P];
+    const int nx = *xn;  // the same for every lane
 #pragma unroll
     for (int p = 0; p < P; ++p)
         e[p] = lane + 32 * p < xe ? xl[lane + 32 * p] : make_uint2(0u, 0u);
+    const uint2 ex = lane < nx ? xx[lane] : make_uint2(0u, 0u);
     const uint32_t kb = __float_as_uint(*xb) | 0x80000000u;  // ord_key of the bound (>= 0)
     uint32_t bk = 0u, bv = 0xFFFFFFFFu;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const uint32_t v = e[p].y;
-        const uint32_t word = tb.word_of((int)v);
-        const bool ok = lane + 32 * p < xe && !((word >> (v & 31)) & 1u);
-        const uint32_t k = ok ? (e[p].x | 0x80000000u) : 0u;  // ord_key of choice_info >= 0
-        if (k > bk || (k == bk && k != 0u && v < bv)) {
-            bk = k;
-            bv = v;
-        }
-    }
+    for (int p = 0; p < P; ++p) reach_entry<TW>(e[p], lane + 32 * p < xe, tb, bk, bv);
+    if (nx > 0) reach_entry<TW>(ex, lane < nx, tb, bk, bv);
     const uint32_t mx = __reduce_max_sync(FULL, bk);
     if (mx <= kb) return -1;  // no unvisited listed node, or one outside may be as good
     return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
@@ -210,16 +220,17 @@ __device__ __forceinline__ int greedy_reach(const uint2 *__restrict__ xl, const 
 // trip: on clustered instances most fallbacks come early in the tour, with
 // thousands of nodes unvisited, where gathering only the unvisited entries
 // costs many more round trips.
-// xl / xb: cur's reach list and bound (xe = 0: none).
+// xl / xb / xx / xn: cur's reach list, bound and extra list (xe = 0: none).
 template <int TW>
 __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, const Tabu<TW> tb,
                                           int lane, int mode, uint32_t t, uint32_t ant, uint32_t it,
                                           uint32_t k0, uint32_t k1, uint32_t *err, int cur,
-                                          const uint2 *xl, const float *xb, int xe)
+                                          const uint2 *xl, const float *xb, const uint2 *xx,
+                                          const int32_t *xn, int xe)
 {
     if (mode == 0) {
         if (xe > 0) {
-            const int r = greedy_reach<TW>(xl, xb, xe, tb, lane);
+            const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane);
             if (r >= 0) return r;
         }
         return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
@@ -263,7 +274,8 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     ++fbn;
     return cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                              (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
-                             a.xlw + (size_t)cur * a.xe, a.xlb + cur, a.xe);
+                             a.xlw + (size_t)cur * a.xe, a.xlb + cur,
+                             a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe);
 }
 
 // Store the window of steps [32w, t_end]: lane l holds entry 32w + l.
@@ -363,7 +375,8 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         const int t = 4 * g + jfail;
         const int fb = cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
                                          (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
-                                         cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur, a.xe);
+                                         cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
+                                         a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
         cur = fb;

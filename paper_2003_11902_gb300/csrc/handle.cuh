@@ -33,6 +33,9 @@ struct mmas_handle {
     int32_t *xl32 = nullptr;         // [n][xe]
     uint2 *xlw = nullptr;            // [n][xe]
     float *xlb = nullptr;            // [n]
+    uint2 *xxw = nullptr;            // [n][REACH_EXTRA]
+    int32_t *xxn = nullptr;          // [n]
+    int32_t *xhot = nullptr;         // [n]
     mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
     int32_t *h_tour = nullptr;      // pinned staging of the best tour
 

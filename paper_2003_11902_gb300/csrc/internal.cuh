@@ -205,11 +205,16 @@ struct ConstructArgs {
     int32_t xe;
     const uint2 *xlw;          // [n][xe] {float bits of choice_info, node}
     const float *xlb;          // [n]
+    const uint2 *xxw;          // [n][REACH_EXTRA] nodes outside the list above the trail floor
+    const int32_t *xxn;        // [n] how many of them are stored
 };
 
 // Longest reach list of the greedy fallback (lane l of a warp holds entries
 // l, l + 32, l + 64, l + 96).
 constexpr int REACH_MAX = 128;
+// Nodes outside the reach list whose trail is above tau_min, stored per row
+// beside it (lane l holds one); the bound covers the rest.
+constexpr int REACH_EXTRA = 32;
 
 // One unit of batched construction: ants first .. first+count-1 of a colony.
 struct BatchChunk {
@@ -262,7 +267,11 @@ struct UpdateArgs {
     int32_t xe;
     const int32_t *xl32;  // [n][xe] the xe nearest nodes of each row, (d, id) order
     uint2 *xlw;           // [n][xe] {float bits of choice_info, node}
-    float *xlb;           // [n] max choice_info over j != i with eta^beta_ij <= that of the last listed node
+    uint2 *xxw;           // [n][REACH_EXTRA] up to REACH_EXTRA such nodes with tau > tau_min
+    int32_t *xxn;         // [n] how many are stored (0: the list is unused)
+    int32_t *xhot;        // [n] nodes above tau_min outside the list at the last pass
+    float *xlb;           // [n] max choice_info over the other nodes j != i with eta^beta_ij at
+                          // most that of the last listed node
 };
 
 // Message returned by mmas_last_error(NULL) on the calling thread.

@@ -189,12 +189,24 @@ __global__ void __launch_bounds__(256)
 // whose eta^beta does not exceed the last listed node's: every node outside
 // the list is among them (eta^beta does not increase with distance beyond the
 // list), so this bounds their choice_info for the greedy fallback.
-template <bool FULLROW, bool ALPHA1>
+template <bool FULLROW, bool ALPHA1, bool EXTRAS>
 __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmin, float tmax,
                                            float delta)
 {
-    __shared__ uint32_t s_bound[8];
+    __shared__ uint32_t s_bound[8], s_ball[8];
+    __shared__ int s_nx, s_hot[8];
     const bool reach = !FULLROW && a.xe > 0;
+    // the extra list (xhot set) is filled only for rows that had few nodes
+    // above the trail floor outside the list at the last pass (that changes
+    // slowly); the others just count theirs
+    const bool extras = EXTRAS && reach && a.xhot != nullptr;
+    const bool gather_hot = extras && a.xhot[i] <= 2 * REACH_EXTRA;
+    if (gather_hot) {  // the same for the whole CTA
+        if (threadIdx.x == 0) s_nx = 0;
+        __syncthreads();
+    }
+    float bound_all = 0.0f;
+    int hot_cnt = 0;
     // no node lies outside a list of all n - 1 others
     const float thr = (reach && a.xe < a.n - 1)
                           ? __ldg(a.eb + (size_t)i * a.ld + a.xl32[(size_t)i * a.xe + a.xe - 1])
@@ -221,19 +233,36 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
         for (int c = 0; c < 4; ++c) {
             const int j = (q << 2) + c;
             float x = tv[c];
+            float w = 0.0f;
             if (j < a.n) {
                 if (a.evaporate) {
                     x = fminf(fmaxf(__fmul_rn(x, a.persist), tmin), tmax);
                     if (j == succ || j == pred) x = fminf(__fadd_rn(x, delta), tmax);
                 }
-                const float w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
+                w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
                 wv[c] = (FULLROW && a.recip) ? __frcp_rn(w) : w;
-                if (!FULLROW && j != i && ev[c] <= thr) bound = fmaxf(bound, w);
             } else {
                 x = 0.0f;
                 wv[c] = 0.0f;
             }
             tv[c] = x;
+            if (!FULLROW && reach && j < a.n && j != i && ev[c] <= thr) {
+                // outside the list: a node above the trail floor is stored while
+                // room is left; `bound` covers the others, `bound_all` all
+                bool stored = false;
+                if (extras && x > tmin) {
+                    ++hot_cnt;
+                    if (gather_hot && *reinterpret_cast<volatile int *>(&s_nx) < REACH_EXTRA) {
+                        const int slot = atomicAdd(&s_nx, 1);
+                        if (slot < REACH_EXTRA) {
+                            a.xxw[(size_t)i * REACH_EXTRA + slot] = make_uint2(__float_as_uint(w), (uint32_t)j);
+                            stored = true;
+                        }
+                    }
+                }
+                if (!stored) bound = fmaxf(bound, w);
+                if (EXTRAS) bound_all = fmaxf(bound_all, w);
+            }
         }
         trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
         wrow[q] = make_float4(wv[0], wv[1], wv[2], wv[3]);
@@ -242,6 +271,14 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
         if (reach) {  // choice_info >= 0: its bits order like the values
             const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
             if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = wmax;
+            if (extras) {
+                const uint32_t amax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_all));
+                const int hots = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)hot_cnt);
+                if ((threadIdx.x & 31) == 0) {
+                    s_ball[threadIdx.x >> 5] = amax;
+                    s_hot[threadIdx.x >> 5] = hots;
+                }
+            }
         }
         __syncthreads();  // this row's choice_info is written and visible to the CTA
         const float *w1 = a.wmat + (size_t)i * a.ld;
@@ -255,9 +292,22 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
                 a.xlw[(size_t)i * a.xe + e] = make_uint2(__float_as_uint(w1[v]), (uint32_t)v);
             }
             if (threadIdx.x == 0) {
-                uint32_t m = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_bound[w] > m ? s_bound[w] : m;
-                a.xlb[i] = __uint_as_float(m);
+                uint32_t m = 0, ma = 0;
+                int hots = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    m = s_bound[w] > m ? s_bound[w] : m;
+                    if (extras) {
+                        ma = s_ball[w] > ma ? s_ball[w] : ma;
+                        hots += s_hot[w];
+                    }
+                }
+                // every node above the floor stored: the extra list is exact and
+                // the bound covers the rest; else the list is unused (without
+                // the extra list, bound already covers every outside node)
+                const bool all = gather_hot && hots <= REACH_EXTRA;
+                a.xlb[i] = __uint_as_float(all || !extras ? m : ma);
+                a.xxn[i] = all ? hots : 0;
+                if (extras) a.xhot[i] = hots;
             }
             __syncthreads();  // s_bound is read before the CTA's next row writes it
         }
@@ -265,21 +315,21 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
 }
 
 template <bool FULLROW, bool ALPHA1>
-__global__ void __launch_bounds__(256) k_update(const UpdateArgs a)
+__global__ void __launch_bounds__(256, 4) k_update(const UpdateArgs a)
 {
     const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
-    for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row<FULLROW, ALPHA1>(a, i, tmin, tmax, delta);
+    for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta);
 }
 
 // Batched fused pass (NEXT-2): one CTA per row of every colony.
 template <bool ALPHA1>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_update_batch(const UpdateArgs *__restrict__ args, const int32_t *__restrict__ row_colony,
                    const int32_t *__restrict__ row_base)
 {
     const int b = row_colony[blockIdx.x];
     const UpdateArgs a = args[b];
-    update_row<false, ALPHA1>(a, (int)blockIdx.x - row_base[b], a.sc->tmin, a.sc->tmax, a.sc->delta);
+    update_row<false, ALPHA1, false>(a, (int)blockIdx.x - row_base[b], a.sc->tmin, a.sc->tmax, a.sc->delta);
 }
 
 }  // namespace

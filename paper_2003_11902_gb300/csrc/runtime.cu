@@ -68,7 +68,7 @@ void free_all(mmas_handle *h)
     void *bufs[] = {h->xy,      h->dist,   h->eb,      h->tau,     h->wmat, h->cwinv,
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
                     h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->nnd,
-                    h->xl32,    h->xlw,    h->xlb};
+                    h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -283,6 +283,9 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
         CK(h, dalloc(&h->xl32, (size_t)n * h->xe * sizeof(int32_t), h->stream));
         CK(h, dalloc(&h->xlw, (size_t)n * h->xe * sizeof(uint2), h->stream));
         CK(h, dalloc(&h->xlb, (size_t)n * sizeof(float), h->stream));
+        CK(h, dalloc(&h->xxw, (size_t)n * REACH_EXTRA * sizeof(uint2), h->stream));
+        CK(h, dalloc(&h->xxn, (size_t)n * sizeof(int32_t), h->stream));
+        CK(h, dalloc(&h->xhot, (size_t)n * sizeof(int32_t), h->stream));
         CK(h, launch_candidates(h->dist, n, ld, h->xe, h->xl32, nullptr, s));
     }
     CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, s));
@@ -303,7 +306,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.iter = &h->sc->iter;
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
     ca.tours = h->tours; ca.sc = h->sc;
-    ca.xe = h->xe; ca.xlw = h->xlw; ca.xlb = h->xlb;
+    ca.xe = h->xe; ca.xlw = h->xlw; ca.xlb = h->xlb; ca.xxw = h->xxw; ca.xxn = h->xxn;
     ca.stage_w_bytes = (uint32_t)cw_bytes;
     ca.stage_c_bytes = (uint32_t)cc_bytes;
     if (cl == 0) { ca.stage_w_bytes = 0; ca.stage_c_bytes = 0; }
@@ -337,7 +340,8 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ua.alpha = h->p.alpha;
     ua.eb = h->eb; ua.tau = h->tau; ua.wmat = h->wmat; ua.cand32 = h->cand32; ua.cwinv = h->cwinv;
     ua.nbr = h->nbr; ua.sc = h->sc;
-    ua.xe = h->xe; ua.xl32 = h->xl32; ua.xlw = h->xlw; ua.xlb = h->xlb;
+    ua.xe = h->xe; ua.xl32 = h->xl32; ua.xlw = h->xlw; ua.xlb = h->xlb; ua.xxw = h->xxw; ua.xxn = h->xxn;
+    ua.xhot = h->xhot;
 
     // choice_info of the initial pheromone
     UpdateArgs refresh = ua;
