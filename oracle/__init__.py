@@ -90,6 +90,7 @@ def lib():
                 "orc_colony_construct": (i64, [vp, i32, i32, P(i32), P(i64)]),
                 "orc_colony_iterate": (None, [vp, i32]),
                 "orc_colony_update": (None, [vp, P(i32), i64]),
+                "orc_colony_set_pheromone": (None, [vp, P(f32), f32, f32]),
                 "orc_colony_iter": (i32, [vp]),
                 "orc_colony_nn_len": (i64, [vp]),
                 "orc_colony_best": (i64, [vp, P(i32)]),
@@ -315,6 +316,11 @@ class Colony:
         """Alg. 1 after construction, with a given iteration-best tour."""
         t = np.ascontiguousarray(ib_tour, dtype=np.int32)
         lib().orc_colony_update(self._h, _i32p(t), int(ib_len))
+
+    def set_pheromone(self, tau, tmin, tmax):
+        """Start from pheromone `tau` (n x n) and limits; choice_info follows."""
+        t = np.ascontiguousarray(tau, dtype=np.float32)
+        lib().orc_colony_set_pheromone(self._h, _f32p(t), float(tmin), float(tmax))
 
     def best(self):
         tour = np.zeros(self.n, dtype=np.int32)

@@ -707,6 +707,16 @@ ORC_API int64_t orc_colony_best(const orc_colony *c, int32_t *tour)
     if (tour && c->has_best) memcpy(tour, c->best_tour, sizeof(int32_t) * (size_t)c->n);
     return c->has_best ? c->best_len : -1;
 }
+/* Replace the pheromone (n x n) and the trail limits, then choice_info, as
+ * the set-up does: a state for tests to start the colony from. */
+ORC_API void orc_colony_set_pheromone(orc_colony *c, const float *tau, float tmin, float tmax)
+{
+    memcpy(c->tau, tau, sizeof(float) * (size_t)c->n * c->n);
+    c->tmin = tmin;
+    c->tmax = tmax;
+    orc_choice(c->n, c->tau, c->eb, c->alpha, c->choice);
+}
+
 ORC_API void orc_colony_limits(const orc_colony *c, float *tmin, float *tmax)
 {
     *tmin = c->tmin;

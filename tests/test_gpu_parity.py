@@ -158,6 +158,48 @@ def test_greedy_fallback_after_deposits_matches_oracle(n, cl, kind):
     g.close()
 
 
+@pytest.mark.parametrize("n,cl,kind", [(700, 6, "uniform"), (1500, 8, "clustered")])
+def test_greedy_fallback_on_a_converged_trail_matches_oracle(n, cl, kind):
+    """A converged-looking trail: tau_min everywhere, tau_max on a tour, and a
+    few long edges per node at intermediate levels (deposits of poor tours).
+    The nodes above the floor outside each reach list are few, so the
+    fallback's extra list decides most steps, long edges winning many."""
+    xy = I.clustered(n, 60 + n) if kind == "clustered" else I.uniform(n, 60 + n)
+    m = 32
+    g, o = _pair(xy=xy, m=m, cl=cl, rho=0.05, seed=9)
+    d = o.state()["d"]
+    tmax = np.float32(1e-3)
+    tmin = np.float32(1e-7)
+    tau = np.full((n, n), tmin, np.float32)
+    t = O.nn_tour(d)[1]
+    tau[t, np.roll(t, -1)] = tmax
+    tau[np.roll(t, -1), t] = tmax
+    rng = np.random.default_rng(n)
+    for _ in range(3):
+        j = rng.permutation(n)
+        lv = (tmin * 10.0 ** rng.uniform(1, 4, n)).astype(np.float32)
+        tau[np.arange(n), j] = np.maximum(tau[np.arange(n), j], lv)
+        tau[j, np.arange(n)] = tau[np.arange(n), j]
+    np.fill_diagonal(tau, tmax)
+    g.set_pheromone(tau, tmin, tmax)
+    g.set_pheromone(tau, tmin, tmax)  # the extra lists fill once a pass has seen few hot nodes
+    o.set_pheromone(tau, tmin, tmax)
+    g.set_iteration(3)
+    it = 3
+    g.construct()
+    tours, lens = g.tours()
+    kinds = []
+    for k in range(m):
+        assert is_permutation(tours[k], n)
+        kinds.append(check_ant(o, it, k, tours[k], lens[k]))
+    fb = g.stats()["fallback_steps"]
+    near = kinds.count("near_tie")
+    print(f"n={n} cl={cl} {kind}: {fb} fallback steps in {m} tours, {near} near-tie divergences")
+    assert fb > m
+    assert near <= max(1, m // 50)
+    g.close()
+
+
 def test_lockstep_iterations_match_oracle():
     """Whole-run parity: as long as every pick agrees, tours, lengths, limits,
     best tour and pheromone agree after every iteration."""

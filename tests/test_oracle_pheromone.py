@@ -88,3 +88,15 @@ def test_repeated_update_converges_to_the_limits():
     assert abs(tau[0, 1] / tmax - 1.0) < 1e-4
     assert tau[0, 2] == tmin
     assert np.all(tau <= tmax) and np.all(tau >= tmin)
+
+
+def test_colony_set_pheromone_sets_the_state():
+    n = 40
+    col = O.Colony(xy=I.uniform(n, 5), m=4, cl=8, alpha=1.0)
+    tau = I.random_pheromone(n, 11, 1e-5, 1e-3)
+    col.set_pheromone(tau, np.float32(1e-5), np.float32(1e-3))
+    st = col.state()
+    assert np.array_equal(st["tau"], tau)
+    assert col.limits() == (np.float32(1e-5), np.float32(1e-3))
+    # alpha = 1: choice_info is the single-precision product, as the pass computes it
+    assert np.array_equal(st["choice"], (tau * st["eta_beta"]).astype(np.float32))
