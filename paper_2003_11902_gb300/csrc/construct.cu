@@ -268,7 +268,7 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     if (act) cand_load<PART>(a, cc, cw, cur, cur * a.cl + lane, v, wi);
     const uint32_t word = tb.word_of((int)v);
     const bool ok = act && !((word >> (v & 31)) & 1u);
-    const uint32_t k = ok ? ord_key(__fmul_rn(lg, wi)) : 0u;
+    const uint32_t k = ok ? neg_key(__fmul_rn(lg, wi)) : 0u;
     const uint32_t mx = __reduce_max_sync(FULL, k);
     if (__builtin_expect(mx != 0u, 1)) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
     ++fbn;
@@ -360,7 +360,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         cand_load<PART>(a, cc, cw, cur, idx, v, wi);
         const uint32_t word = tb.word_of((int)v);
         const bool ok = act && !((word >> (v & 31)) & 1u);
-        const uint32_t k = ok ? ord_key(__fmul_rn(lg[j], wi)) : 0u;
+        const uint32_t k = ok ? neg_key(__fmul_rn(lg[j], wi)) : 0u;
         const uint32_t mx = __reduce_max_sync(FULL, k);
         const uint32_t nxt = __reduce_min_sync(FULL, (k == mx && mx != 0u) ? v : 0xFFFFFFFFu);
         jfail = (live && mx == 0u) ? j : jfail;

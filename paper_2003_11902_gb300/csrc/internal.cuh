@@ -85,11 +85,18 @@ __device__ __forceinline__ void philox_rounds_rk(uint4 &c, const uint32_t *rk0, 
     }
 }
 
-// r = ((x >> 9) + 1/2) * 2^-23, exactly representable, in (0, 1).
+// r = ((x >> 9) + 1/2) * 2^-23, exactly representable, in (0, 1): the float
+// with exponent 0 and mantissa x >> 9 is 1 + k 2^-23 (k = x >> 9), and
+// subtracting 1 - 2^-24 from it is exact (Sterbenz), leaving k 2^-23 + 2^-24.
 __device__ __forceinline__ float unit_open(uint32_t x)
 {
-    return __fmul_rn(__fadd_rn((float)(x >> 9), 0.5f), 1.1920928955078125e-7f);
+    return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.99999994039535522461f);
 }
+
+// Order-preserving map of a negative float to uint32 (larger float -> larger
+// code), for the reservoir keys log2(r) / w, which are negative (r < 1, w > 0);
+// the codes are >= 1, so 0 still marks "no candidate".
+__device__ __forceinline__ uint32_t neg_key(float f) { return ~__float_as_uint(f); }
 
 // Order-preserving map of a float to uint32 (larger float -> larger code).
 // Codes are >= 1 for every non-NaN float, so 0 marks "no candidate".
