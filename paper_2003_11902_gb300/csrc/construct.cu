@@ -329,7 +329,8 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
 // interleave.  Only a frozen group leaves the block: that step takes the
 // out-of-line fallback and the group's remaining steps run one by one.  The
 // result equals cand_group's step for step.
-template <int TW, bool PART>
+// CL32: cl = 32, every lane holds a candidate.
+template <int TW, bool PART, bool CL32>
 __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const uint16_t *cc,
                                                 const float *cw, Tabu<TW> &tb, int lane,
                                                 int ant, uint32_t it, int g, float (&lg)[4],
@@ -338,7 +339,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
     uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
     float nl[4];
     const int tb32 = (4 * g) & 31;
-    const bool act = lane < a.cl;
+    const bool act = CL32 || lane < a.cl;
     bool live = true;  // warp-uniform
     int jfail = 4;
 #pragma unroll
@@ -354,7 +355,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
             nl[2] = log2f(unit_open(nx.z));
             nl[3] = log2f(unit_open(nx.w));
         }
-        const int idx = act ? cur * a.cl + lane : 0;
+        const int idx = CL32 ? cur * 32 + lane : (act ? cur * a.cl + lane : 0);
         uint32_t v;
         float wi;
         cand_load<PART>(a, cc, cw, cur, idx, v, wi);
@@ -362,7 +363,8 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         const bool ok = act && !((word >> (v & 31)) & 1u);
         const uint32_t k = ok ? neg_key(__fmul_rn(lg[j], wi)) : 0u;
         const uint32_t mx = __reduce_max_sync(FULL, k);
-        const uint32_t nxt = __reduce_min_sync(FULL, (k == mx && mx != 0u) ? v : 0xFFFFFFFFu);
+        // (when mx = 0 the step freezes and nxt is not used)
+        const uint32_t nxt = __reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
         jfail = (live && mx == 0u) ? j : jfail;
         live = live && mx != 0u;
         tb.mark_if(lane, (int)nxt, live);
@@ -426,7 +428,10 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
         cand_group<true, TW, PART>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
         int g = 1;
         for (; 4 * g + 3 <= a.n - 1; ++g) {
-            cand_group_spec<TW, PART>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
+            if (a.cl == 32)
+                cand_group_spec<TW, PART, true>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
+            else
+                cand_group_spec<TW, PART, false>(a, cc, cw, tb, lane, ant, it, g, lg, cur, twin, fbn);
             if ((g & 7) == 7) store_window(trow, lane, g >> 3, 4 * g + 3, twin);
         }
         if (4 * g <= a.n - 1)
