@@ -396,6 +396,82 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
     for (int j = 0; j < 4; ++j) lg[j] = nl[j];
 }
 
+// Whole-row draws of step t for this lane's chunks c = lane + 32u (nodes
+// 4c .. 4c+3): the log2 of the four words of Philox(2^31 | c, t, ant, it).
+template <int U>
+__device__ __forceinline__ void row_draws(int nch, int lane, uint32_t t, uint32_t ant, uint32_t it,
+                                          uint32_t k0, uint32_t k1, float (&lg)[U][4])
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int c = lane + 32 * u;
+        uint4 r = make_uint4(0x80000000u | (uint32_t)(c < nch ? c : 0), t, ant, it);
+        philox_rounds<0, 10>(r, k0, k1);
+        lg[u][0] = log2f(unit_open(r.x));
+        lg[u][1] = log2f(unit_open(r.y));
+        lg[u][2] = log2f(unit_open(r.z));
+        lg[u][3] = log2f(unit_open(r.w));
+    }
+}
+
+// Whole-row tour for rows of at most 128 U nodes (one pass of U 16-byte
+// chunks per lane): the draws do not depend on the path, so the next step's
+// are computed while the current step scans, and the step itself is one
+// straight block of U chunk loads, key products and a two-step reduction.
+// The same picks as scan_row (ties -> lower id).
+template <int U, int TW>
+__device__ __forceinline__ void row_tour_pipelined(const ConstructArgs &a, const float *cw, Tabu<TW> &tb,
+                                                   int lane, int ant, uint32_t it, int32_t *trow,
+                                                   int &cur, int &twin)
+{
+    const int n = a.n, nch = (n + 3) >> 2;
+    float lg[U][4], ln[U][4];
+    row_draws<U>(nch, lane, 1u, (uint32_t)ant, it, a.key0, a.key1, lg);
+    for (int t = 1; t < n; ++t) {
+        const float *row = cw + (size_t)cur * a.ld;
+        float4 w4[U];
+        uint32_t bits[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = lane + 32 * u;
+            const int v0 = c << 2;
+            const uint32_t word = tb.word_of(v0 < n ? v0 : n - 1);
+            bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
+            w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        row_draws<U>(nch, lane, (uint32_t)(t + 1), (uint32_t)ant, it, a.key0, a.key1, ln);
+        uint32_t bk = 0u, bv = 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v0 = (lane + 32 * u) << 2;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const bool ok = v0 + e < n && !((bits[u] >> e) & 1u);
+                const uint32_t kk = ok ? neg_key(__fmul_rn(lg[u][e], pick_f(w4[u], e))) : 0u;
+                if (kk > bk) {  // ascending nodes: ties keep the lower id
+                    bk = kk;
+                    bv = (uint32_t)(v0 + e);
+                }
+            }
+        }
+        const uint32_t mx = __reduce_max_sync(FULL, bk);
+        int next = cur;
+        if (mx == 0u) {
+            if (lane == 0) atomicOr(&a.sc->err, ERR_NO_UNVISITED);
+        } else {
+            next = (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+        }
+        tb.mark(lane, next);
+        twin = (lane == (t & 31)) ? next : twin;
+        if ((t & 31) == 31 || t == n - 1) store_window(trow, lane, t >> 5, t, twin);
+        cur = next;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) lg[u][e] = ln[u][e];
+    }
+}
+
 // Build the tour of ant `ant` (its global index, which keys the draws) into
 // trow: a uniform start (Alg. 1), then n - 1 selections.  `it` is the
 // iteration index; cc / cw are the candidate table (staged or global) or the
@@ -438,6 +514,8 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
             cand_group<true, TW, PART>(a, cc, cw, tb, trow, lane, ant, it, g, lg, cur, twin, fbn);
         else if (g > 1 && ((g - 1) & 7) != 7)
             store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
+    } else if (a.n <= 256) {
+        row_tour_pipelined<2, TW>(a, cw, tb, lane, ant, it, trow, cur, twin);
     } else {
         for (int t = 1; t < a.n; ++t) {
             const int next = scan_row<TW, false, true>(cw + (size_t)cur * a.ld, a.n, tb, lane,
