@@ -516,6 +516,10 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
             store_window(trow, lane, (g - 1) >> 3, a.n - 1, twin);  // last full group ended it
     } else if (a.n <= 256) {
         row_tour_pipelined<2, TW>(a, cw, tb, lane, ant, it, trow, cur, twin);
+    } else if (a.n <= 512) {
+        row_tour_pipelined<4, TW>(a, cw, tb, lane, ant, it, trow, cur, twin);
+    } else if (a.n <= 1024) {
+        row_tour_pipelined<8, TW>(a, cw, tb, lane, ant, it, trow, cur, twin);
     } else {
         for (int t = 1; t < a.n; ++t) {
             const int next = scan_row<TW, false, true>(cw + (size_t)cur * a.ld, a.n, tb, lane,
