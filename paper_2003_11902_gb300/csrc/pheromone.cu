@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(256)
 // the list is among them (eta^beta does not increase with distance beyond the
 // list), so this bounds their choice_info for the greedy fallback.
 template <bool FULLROW, bool ALPHA1, bool EXTRAS>
-__device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmin, float tmax,
-                                           float delta)
+__device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float tmin, float tmax,
+                                               float delta)
 {
     __shared__ uint32_t s_bound[8], s_ball[8];
     __shared__ int s_nx, s_hot[8];
@@ -314,22 +314,149 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
     }
 }
 
+// One CTA per row: for colonies with few rows, where every row's latency counts.
+template <bool FULLROW, bool ALPHA1>
+__global__ void __launch_bounds__(256, 4) k_update_cta(const UpdateArgs a)
+{
+    const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
+    for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row_cta<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta);
+}
+
+// The same pass with one warp per row (slots of the extra list by ballot),
+// for colonies of many rows and for the batched pass: no CTA barrier, and the
+// latency of a row is hidden by the other rows of the SM.
+template <bool FULLROW, bool ALPHA1, bool EXTRAS>
+__device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmin, float tmax,
+                                           float delta, int lane)
+{
+    const bool reach = !FULLROW && a.xe > 0;
+    // the extra list (xhot set) is filled only for rows that had few nodes
+    // above the trail floor outside the list at the last pass (that changes
+    // slowly); the others just count theirs
+    const bool extras = EXTRAS && reach && a.xhot != nullptr;
+    const bool gather_hot = extras && a.xhot[i] <= 2 * REACH_EXTRA;
+    // no node lies outside a list of all n - 1 others
+    const float thr = (reach && a.xe < a.n - 1)
+                          ? __ldg(a.eb + (size_t)i * a.ld + a.xl32[(size_t)i * a.xe + a.xe - 1])
+                          : -1.0f;
+    float bound = 0.0f, bound_all = 0.0f;
+    int hot_cnt = 0, nx = 0;  // nx: extras stored so far (the same in every lane)
+    const unsigned below = (1u << lane) - 1u;
+    const int nq = a.ld >> 2;
+    int succ = -1, pred = -1;
+    if (a.nbr) {
+        const int2 nb = a.nbr[i];
+        succ = nb.x;
+        pred = nb.y;
+    }
+    float4 *trow = reinterpret_cast<float4 *>(a.tau + (size_t)i * a.ld);
+    const float4 *erow = reinterpret_cast<const float4 *>(a.eb + (size_t)i * a.ld);
+    float4 *wrow = reinterpret_cast<float4 *>(a.wmat + (size_t)i * a.ld);
+    for (int q0 = 0; q0 < nq; q0 += 32) {  // every lane takes each round
+        const int q = q0 + lane;
+        const bool inq = q < nq;
+        const float4 t4 = inq ? trow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 e4 = inq ? __ldg(erow + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+        const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+        float wv[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = (q << 2) + c;
+            float x = tv[c];
+            float w = 0.0f;
+            if (j < a.n) {
+                if (a.evaporate) {
+                    x = fminf(fmaxf(__fmul_rn(x, a.persist), tmin), tmax);
+                    if (j == succ || j == pred) x = fminf(__fadd_rn(x, delta), tmax);
+                }
+                w = ALPHA1 ? __fmul_rn(x, ev[c]) : __fmul_rn(powf(x, a.alpha), ev[c]);
+                wv[c] = (FULLROW && a.recip) ? __frcp_rn(w) : w;
+            } else {
+                x = 0.0f;
+                wv[c] = 0.0f;
+            }
+            tv[c] = x;
+            if (!FULLROW && reach) {
+                // outside the list: a node above the trail floor is stored while
+                // room is left (slots by warp ballot); `bound` covers the
+                // others, `bound_all` all of them
+                const bool outside = j < a.n && j != i && ev[c] <= thr;
+                const bool hot = extras && outside && x > tmin;
+                hot_cnt += hot ? 1 : 0;
+                bool stored = false;
+                if (gather_hot) {  // the same in every lane
+                    const unsigned hm = __ballot_sync(0xFFFFFFFFu, hot);
+                    if (hot) {
+                        const int slot = nx + __popc(hm & below);
+                        if (slot < REACH_EXTRA) {
+                            a.xxw[(size_t)i * REACH_EXTRA + slot] = make_uint2(__float_as_uint(w), (uint32_t)j);
+                            stored = true;
+                        }
+                    }
+                    nx += __popc(hm);
+                }
+                if (outside && !stored) bound = fmaxf(bound, w);
+                if (EXTRAS && outside) bound_all = fmaxf(bound_all, w);
+            }
+        }
+        if (inq) {
+            trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+            wrow[q] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        }
+    }
+    if (!FULLROW && a.cl > 0) {
+        __syncwarp();  // the row's choice_info, written by this warp, is visible to its lanes
+        const float *w1 = a.wmat + (size_t)i * a.ld;
+        for (int c = lane; c < a.cl; c += 32) {
+            const int v = a.cand32[(size_t)i * a.cl + c];
+            a.cwinv[(size_t)i * a.cl + c] = __frcp_rn(w1[v]);
+        }
+        if (reach) {
+            for (int e = lane; e < a.xe; e += 32) {
+                const int v = a.xl32[(size_t)i * a.xe + e];
+                a.xlw[(size_t)i * a.xe + e] = make_uint2(__float_as_uint(w1[v]), (uint32_t)v);
+            }
+            // choice_info >= 0: its bits order like the values
+            const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
+            const uint32_t ma = extras ? __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_all)) : 0u;
+            const int hots = extras ? (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)hot_cnt) : 0;
+            if (lane == 0) {
+                // every node above the floor stored: the extra list is exact and
+                // the bound covers the rest; else the list is unused (without
+                // the extra list, bound already covers every outside node)
+                const bool all = gather_hot && hots <= REACH_EXTRA;
+                a.xlb[i] = __uint_as_float(all || !extras ? m : ma);
+                a.xxn[i] = all ? hots : 0;
+                if (extras) a.xhot[i] = hots;
+            }
+        }
+    }
+}
+
+// One warp per row, eight rows per CTA.
 template <bool FULLROW, bool ALPHA1>
 __global__ void __launch_bounds__(256, 4) k_update(const UpdateArgs a)
 {
     const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
-    for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < a.n; i += nwarps)
+        update_row<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta, lane);
 }
 
-// Batched fused pass (NEXT-2): one CTA per row of every colony.
+// Batched fused pass (NEXT-2): one warp per row of every colony.
 template <bool ALPHA1>
 __global__ void __launch_bounds__(256, 4)
     k_update_batch(const UpdateArgs *__restrict__ args, const int32_t *__restrict__ row_colony,
-                   const int32_t *__restrict__ row_base)
+                   const int32_t *__restrict__ row_base, int total_rows)
 {
-    const int b = row_colony[blockIdx.x];
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= total_rows) return;
+    const int b = row_colony[row];
     const UpdateArgs a = args[b];
-    update_row<false, ALPHA1, false>(a, (int)blockIdx.x - row_base[b], a.sc->tmin, a.sc->tmax, a.sc->delta);
+    update_row<false, ALPHA1, false>(a, row - row_base[b], a.sc->tmin, a.sc->tmax, a.sc->delta,
+                                     threadIdx.x & 31);
 }
 
 }  // namespace
@@ -364,17 +491,30 @@ cudaError_t launch_score_batch(const ScoreArgs *args, const int32_t *ant_colony,
 cudaError_t launch_update_batch(const UpdateArgs *args, const int32_t *row_colony, const int32_t *row_base,
                                 int total_rows, bool alpha1, cudaStream_t s)
 {
+    const int grid = (total_rows + 7) / 8;
     if (alpha1)
-        k_update_batch<true><<<total_rows, 256, 0, s>>>(args, row_colony, row_base);
+        k_update_batch<true><<<grid, 256, 0, s>>>(args, row_colony, row_base, total_rows);
     else
-        k_update_batch<false><<<total_rows, 256, 0, s>>>(args, row_colony, row_base);
+        k_update_batch<false><<<grid, 256, 0, s>>>(args, row_colony, row_base, total_rows);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s)
 {
-    const int grid = a.n < num_sms * 8 ? a.n : num_sms * 8;
     const bool a1 = a.alpha == 1.0f;
+    if (a.n <= 8192) {  // a CTA per row: few rows, each one's latency counts
+        const int grid = a.n < num_sms * 8 ? a.n : num_sms * 8;
+        if (a.fullrow) {
+            if (a1) k_update_cta<true, true><<<grid, 256, 0, s>>>(a);
+            else k_update_cta<true, false><<<grid, 256, 0, s>>>(a);
+        } else {
+            if (a1) k_update_cta<false, true><<<grid, 256, 0, s>>>(a);
+            else k_update_cta<false, false><<<grid, 256, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    const int rows8 = (a.n + 7) / 8;  // eight rows (warps) per CTA
+    const int grid = rows8 < num_sms * 8 ? rows8 : num_sms * 8;
     if (a.fullrow) {
         if (a1) k_update<true, true><<<grid, 256, 0, s>>>(a);
         else k_update<true, false><<<grid, 256, 0, s>>>(a);
