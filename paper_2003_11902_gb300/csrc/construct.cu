@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
         build_tour<MODE, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
 }
 
-// Batched construction (NEXT-2): one persistent launch builds every ant of
+// Batched construction: one persistent launch builds every ant of
 // every colony.  A CTA repeatedly takes the next chunk (one colony, up to one
 // ant per warp) from a global counter -- the chunk list is ordered by
 // decreasing n so the longest tours start first -- loads that colony's

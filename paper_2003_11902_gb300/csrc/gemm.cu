@@ -1,5 +1,5 @@
 // BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05 / UMMA),
-// FP32 accumulation in tensor memory, for the learned edge prior (NEXT-3):
+// FP32 accumulation in tensor memory, for the learned edge prior:
 //
 //   D[M x N] = act(A[M x K] * B[N x K]^T + bias[N])   (+ optional residual R[M x N])
 //

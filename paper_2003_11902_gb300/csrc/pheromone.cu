@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_score(const ScoreArgs a)
     if (tid == 0) a.b.sc->done = 0;
 }
 
-// Batched lengths (NEXT-2): one CTA per ant of every colony; the last CTA of a
+// Batched lengths: one CTA per ant of every colony; the last CTA of a
 // colony to finish runs that colony's select_best.
 template <bool XY>
 __global__ void __launch_bounds__(256)
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(256, 4) k_update(const UpdateArgs a)
         update_row<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta, lane);
 }
 
-// Batched fused pass (NEXT-2): one warp per row of every colony.
+// Batched fused pass: one warp per row of every colony.
 template <bool ALPHA1>
 __global__ void __launch_bounds__(256, 4)
     k_update_batch(const UpdateArgs *__restrict__ args, const int32_t *__restrict__ row_colony,
