@@ -733,6 +733,52 @@ __device__ __forceinline__ float rwm_scan(float S, int lane)
     return S;
 }
 
+// The same procedure for N <= 128 RC: the first pass keeps each round's
+// weights, partial sums and lane scan in registers, so the search pass reuses
+// them instead of reloading and rescanning (the same operations, the same pick).
+template <int RC, class X>
+__device__ __forceinline__ int rwm_pick_cached(X x, int N, float u, int lane)
+{
+    const int rounds = (N + 127) >> 7;
+    float w[RC][4], q[RC][4], S[RC], P[RC];
+    float total = 0.0f;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        if (r < rounds) {
+            rwm_lane(x, r, lane, N, w[r], q[r]);
+            S[r] = rwm_scan(q[r][3], lane);
+            P[r] = __shfl_up_sync(FULL, S[r], 1);
+            if (lane == 0) P[r] = 0.0f;
+            total = __fadd_rn(total, __shfl_sync(FULL, S[r], 31));
+        }
+    }
+    const float theta = __fmul_rn(u, total);
+    float off = 0.0f;
+    int last = -1;
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        if (r < rounds) {
+            const float base = __fadd_rn(off, P[r]);
+            int hit = 4;
+#pragma unroll
+            for (int e = 3; e >= 0; --e) {
+                const int p = 128 * r + 4 * lane + e;
+                if (p < N && w[r][e] > 0.0f) {
+                    last = p > last ? p : last;
+                    if (__fadd_rn(base, q[r][e]) > theta) hit = e;
+                }
+            }
+            const unsigned b = __ballot_sync(FULL, hit < 4);
+            if (b) {
+                const int wl = __ffs(b) - 1;
+                return 128 * r + 4 * wl + __shfl_sync(FULL, hit, wl);
+            }
+            off = __fadd_rn(off, __shfl_sync(FULL, S[r], 31));
+        }
+    }
+    return (int)__reduce_max_sync(FULL, (unsigned)(last + 1)) - 1;
+}
+
 // The parallel roulette wheel over positions [0, N) with draw u: the exact
 // single-precision procedure (rounds of 128 positions, lane partial sums,
 // lane scan, running round offset; first position whose cumulative sum
@@ -836,7 +882,7 @@ __device__ __forceinline__ void build_tour_var(const ConstructArgs &a, const flo
 #pragma unroll
                     for (int k = 0; k < 4; ++k) w[k] = p0 + k < N ? row[e[p0 + k]] : 0.0f;
                 };
-                nslot = rwm_pick(x, cl.L, u, lane);
+                nslot = cl.L <= 256 ? rwm_pick_cached<2>(x, cl.L, u, lane) : rwm_pick(x, cl.L, u, lane);
                 next = nslot >= 0 ? (int)cl.e[nslot] : -1;
             } else {
                 auto x = [&](int p0, int N, float (&w)[4]) {
@@ -848,7 +894,7 @@ __device__ __forceinline__ void build_tour_var(const ConstructArgs &a, const flo
                     w[2] = p0 + 2 < N && !(bits & 4u) ? v.z : 0.0f;
                     w[3] = p0 + 3 < N && !(bits & 8u) ? v.w : 0.0f;
                 };
-                next = rwm_pick(x, a.n, u, lane);
+                next = a.n <= 256 ? rwm_pick_cached<2>(x, a.n, u, lane) : rwm_pick(x, a.n, u, lane);
             }
         } else {
             // reservoir sampling over the compact list, slot-keyed draws
