@@ -314,13 +314,22 @@ def algorithmic_construct_bytes(w):
     return m * per_ant
 
 
-def time_to_gap(w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=4000):
+# L* of a workload: the oracle's long-run best (tests/golden/make_lstar.py)
+LSTAR_FILES = {"uniform-n1000-cl32": ("lstar_uniform_n1000.json", "seeds 1-3, 1000 iterations"),
+               "clustered-n3800-cl16-2opt": ("lstar_clustered_n3800.json",
+                                             "seeds 1-3, 500 iterations with 2-opt of the iteration best")}
+
+
+def time_to_gap(workload, w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=4000):
     """Wall time from mmas_create until the colony's global best is within `gap`
     of the oracle's long-run best L* (tests/golden), checking every few
     iterations (each check reads the best length back to the host)."""
     from paper_2003_11902_gb300 import Colony
-    path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
-    if w["n"] != 1000 or w["cl"] != 32 or not os.path.exists(path):
+    if workload not in LSTAR_FILES:
+        return None
+    fname, how = LSTAR_FILES[workload]
+    path = os.path.join(ROOT, "tests", "golden", fname)
+    if not os.path.exists(path):
         return None
     with open(path) as f:
         lstar = json.load(f)["lstar"]
@@ -328,7 +337,8 @@ def time_to_gap(w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=400
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, device=dev, stream=stream, **PARAMS)
+    col = Colony(xy=xy, m=w["m"], cl=w["cl"], seed=seed, ls=w.get("ls", 0), device=dev, stream=stream,
+                 **PARAMS)
     it, best = 0, None
     while it < max_iters:
         col.iterate(check_every)
@@ -341,7 +351,7 @@ def time_to_gap(w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=400
     return {"seconds": el if best <= target else None, "iterations": it, "best_len": best,
             "lstar": lstar, "target": target, "seed": seed,
             "timed": f"mmas_create + iterations + a best-length read every {check_every} iterations",
-            "lstar_source": "tests/golden/lstar_uniform_n1000.json (oracle, seeds 1-3, 1000 iterations)"}
+            "lstar_source": f"tests/golden/{fname} (oracle, {how})"}
 
 
 def run_ours(args, w):
@@ -462,7 +472,7 @@ def run_ours(args, w):
                              "occupancy, same run)",
                 "binding": f"neither: the step-to-step dependency chain of each ant (about 300 "
                            f"cycles a step) with {w['m']} ants on {sched} warp schedulers"}
-        gapres = None if args.no_gap else time_to_gap(w, xy, seed, dev, stream.cuda_stream)
+        gapres = None if args.no_gap else time_to_gap(args.workload, w, xy, seed, dev, stream.cuda_stream)
         if gapres is not None:
             line["time_to_2pct_gap"] = gapres
         if ws == 1 and not args.no_cpu_baseline:
