@@ -650,6 +650,8 @@ def run_ours_batch(args, w):
             line["vs_single_colonies"] = _single_colonies(w, xys, seed, dev, stream.cuda_stream,
                                                           args.warmup + args.steps, args.steps,
                                                           total_ms, best)
+            if not args.no_gap:
+                line["time_to_2pct_gap"] = batch_time_to_gap(w, seed, dev, stream.cuda_stream)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_batch(w, xys)
         print(json.dumps(line), flush=True)
@@ -680,6 +682,58 @@ def _single_colonies(w, xys, seed, dev, stream, iters, timed, batch_ms, batch_be
             "speedup": ms / batch_ms, "same_best_lengths": bool(same),
             "note": "device time (CUDA events in each colony's iteration graph); the batch and the "
                     "colonies run alone build the same tours, so any time-to-quality ratio is this one"}
+
+
+def batch_time_to_gap(w, seed, dev, stream, gap=0.02, check_every=5, max_iters=4000):
+    """Wall time for the sampled instances of the batched workload (the oracle's
+    L* of each in tests/golden/lstar_batched_sample16.json) to come within `gap`
+    of their L*: as one batch (create, then iterate until every colony is
+    within), and as plain colonies run one after another (create, then iterate
+    until within; times summed).  Colony b gets seed + b either way, so both
+    build the same tours; every check reads the best lengths back."""
+    import torch
+
+    from paper_2003_11902_gb300 import Batch, Colony
+    from paper_2003_11902_gb300 import instances as I
+    path = os.path.join(ROOT, "tests", "golden", "lstar_batched_sample16.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        insts = json.load(f)["instances"]
+    xys = [I.uniform(e["n"], 1000 + e["index"]) for e in insts]
+    target = np.array([(1.0 + gap) * e["lstar"] for e in insts])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = Batch(xys=xys, m=0, cl=w["cl"], seed=seed, device=dev, stream=stream, **PARAMS)
+    it = 0
+    while it < max_iters:
+        bt.iterate(check_every)
+        it += check_every
+        best = bt.best_lengths()
+        if np.all(best <= target):
+            break
+    batch_s = time.perf_counter() - t0 if np.all(best <= target) else None
+    bt.close()
+    single_s, its = 0.0, []
+    for b, xy in enumerate(xys):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        col = Colony(xy=xy, m=len(xy), cl=w["cl"], seed=seed + b, device=dev, stream=stream, **PARAMS)
+        k = 0
+        while k < max_iters:
+            col.iterate(check_every)
+            k += check_every
+            if col.stats()["best_len"] <= target[b]:
+                break
+        single_s += time.perf_counter() - t0
+        its.append(k)
+        col.close()
+    return {"instances": [[e["index"], e["n"]] for e in insts], "batch_seconds": batch_s,
+            "batch_iterations": it, "single_seconds_total": single_s,
+            "single_iterations": its, "speedup": single_s / batch_s if batch_s else None,
+            "timed": f"create + iterations + a best-length read every {check_every} iterations",
+            "lstar_source": "tests/golden/lstar_batched_sample16.json (oracle, per instance the best of "
+                            "seeds 1-3, 1000 iterations)"}
 
 
 def _race(col, seconds, target, check_every=5):

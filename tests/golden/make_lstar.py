@@ -10,11 +10,17 @@ measurement.  Calls only the oracle.  Workloads:
   clustered-n3800 synthetic clustered n = 3800 (seed 1003), m = 1000, cl = 16,
                   2-opt of each iteration's best (Sec. 5.7), 500 iterations
                   -> lstar_clustered_n3800.json
+  batched-sample16 the first 16 instances with n <= 400 of the batched workload
+                  (256 uniform instances, n = round(exp(U[ln 100, ln 2000])) with
+                  size seed 1000, coordinate seed 1000 + index), m = n, cl = 32,
+                  1000 iterations each -> lstar_batched_sample16.json (one L*
+                  per instance; runs go to a pool of single-threaded processes)
 
     python tests/golden/make_lstar.py [--workload uniform-n1000] [--iters N] [--threads N]
 """
 import argparse
 import json
+import multiprocessing as mp
 import os
 import sys
 import time
@@ -40,12 +46,56 @@ WORKLOADS = {
 }
 
 
+BATCH_SAMPLE = dict(count=256, size_seed=1000, lo=100, hi=2000, max_n=400, take=16, cl=32, iters=1000,
+                    out="lstar_batched_sample16.json")
+
+
+def batch_sample():
+    """(index, n) of the sampled instances of the batched workload."""
+    b = BATCH_SAMPLE
+    ns = I.log_uniform_sizes(b["count"], b["size_seed"], b["lo"], b["hi"])
+    return [(i, int(n)) for i, n in enumerate(ns) if n <= b["max_n"]][:b["take"]]
+
+
+def _run_one(job):
+    idx, n, seed, iters = job
+    xy = I.uniform(n, 1000 + idx)
+    t0 = time.time()
+    col = O.Colony(xy=xy, m=n, cl=BATCH_SAMPLE["cl"], alpha=1.0, beta=2.0, rho=float(np.float32(0.02)),
+                   p_best=float(np.float32(0.01)), seed=seed)
+    col.iterate(iters, threads=1)
+    return idx, seed, int(col.best()[0]), round(time.time() - t0, 1)
+
+
+def main_batch(iters, procs):
+    jobs = [(i, n, seed, iters) for i, n in batch_sample() for seed in (1, 2, 3)]
+    jobs.sort(key=lambda j: -j[1])  # largest first
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = list(pool.imap_unordered(_run_one, jobs))
+    insts = []
+    for i, n in batch_sample():
+        runs = sorted((r for r in res if r[0] == i), key=lambda r: r[1])
+        insts.append({"index": i, "n": n, "lstar": min(r[2] for r in runs),
+                      "runs": [{"seed": r[1], "best": r[2], "seconds": r[3]} for r in runs]})
+        print(i, n, insts[-1]["lstar"], flush=True)
+    b = BATCH_SAMPLE
+    out = {"workload": f"the first {b['take']} instances with n <= {b['max_n']} of the batched workload "
+                       f"({b['count']} uniform instances, sizes log-uniform in [{b['lo']}, {b['hi']}] with "
+                       f"size seed {b['size_seed']}, coordinate seed 1000 + index), m = n, cl = {b['cl']}, "
+                       "alpha=1, beta=2, rho=0.02, p_best=0.01",
+           "iterations": iters, "instances": insts, "source": "tests/golden/make_lstar.py (CPU oracle)"}
+    with open(os.path.join(HERE, b["out"]), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform-n1000")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-sample16"], default="uniform-n1000")
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     args = ap.parse_args()
+    if args.workload == "batched-sample16":
+        return main_batch(args.iters or BATCH_SAMPLE["iters"], args.threads)
     w = WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
     xy = I.uniform(w["n"], w["iseed"]) if w["kind"] == "uniform" else I.clustered(w["n"], w["iseed"])
