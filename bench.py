@@ -317,7 +317,10 @@ def algorithmic_construct_bytes(w):
 # L* of a workload: the oracle's long-run best (tests/golden/make_lstar.py)
 LSTAR_FILES = {"uniform-n1000-cl32": ("lstar_uniform_n1000.json", "seeds 1-3, 1000 iterations"),
                "clustered-n3800-cl16-2opt": ("lstar_clustered_n3800.json",
-                                             "seeds 1-3, 500 iterations with 2-opt of the iteration best")}
+                                             "seeds 1-3, 500 iterations with 2-opt of the iteration best"),
+               "learned-prior-n1000-cl16-2opt": ("lstar_uniform_n1000_cl16_2opt.json",
+                                                 "plain MMAS, seeds 1-3, 1000 iterations with 2-opt of the "
+                                                 "iteration best")}
 
 
 def time_to_gap(workload, w, xy, seed, dev, stream, gap=0.02, check_every=5, max_iters=4000):
@@ -813,10 +816,12 @@ def run_ours_prior(args, w):
     # ---- equal-wall-time race on the evaluation instance
     xy = _instance(w)
     lstar = None
-    if w["n"] == 1000:
-        path = os.path.join(ROOT, "tests", "golden", "lstar_uniform_n1000.json")
-        with open(path) as f:
-            lstar = json.load(f)["lstar"]
+    if args.workload in LSTAR_FILES:
+        fname, how = LSTAR_FILES[args.workload]
+        path = os.path.join(ROOT, "tests", "golden", fname)
+        if os.path.exists(path):
+            with open(path) as f:
+                lstar = json.load(f)["lstar"]
     # three colonies: plain eta^beta, eta^beta replaced by the edge
     # probabilities, and eta^beta weighted by them (gamma = 1)
     plain = Colony(xy=xy, m=w["m"], seed=1, **common)
@@ -836,7 +841,7 @@ def run_ours_prior(args, w):
     # oracle's long-run best) where it is known, else the better final best
     # of the two colonies
     if lstar is not None:
-        target, target_source = 1.02 * lstar, "1.02 L*, L* from tests/golden/lstar_uniform_n1000.json (oracle)"
+        target, target_source = 1.02 * lstar, f"1.02 L*, L* from tests/golden/{fname} (oracle, {how})"
     else:
         target = 1.02 * min(r["best_at_end"] for r in race.values())
         target_source = "1.02 x the better final best of the two colonies (no oracle L* at this size)"

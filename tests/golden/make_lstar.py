@@ -7,6 +7,9 @@ measurement.  Calls only the oracle.  Workloads:
 
   uniform-n1000   synthetic uniform n = 1000 (coordinate seed 1001), m = 1000,
                   cl = 32, 1000 iterations -> lstar_uniform_n1000.json
+  uniform-n1000-cl16-2opt  the same instance, m = 1000, cl = 16, 2-opt of each
+                  iteration's best, 1000 iterations -> lstar_uniform_n1000_cl16_2opt.json
+                  (the plain colony of the learned-prior race at n = 1000)
   clustered-n3800 synthetic clustered n = 3800 (seed 1003), m = 1000, cl = 16,
                   2-opt of each iteration's best (Sec. 5.7), 500 iterations
                   -> lstar_clustered_n3800.json
@@ -39,11 +42,20 @@ WORKLOADS = {
                           out="lstar_uniform_n1000.json",
                           text="uniform n=1000 (coordinate seed 1001), m=1000, cl=32, alpha=1, beta=2, "
                                "rho=0.02, p_best=0.01"),
+    "uniform-n1000-cl16-2opt": dict(kind="uniform", n=1000, iseed=1001, m=1000, cl=16, ls=1, iters=1000,
+                                    out="lstar_uniform_n1000_cl16_2opt.json",
+                                    text="uniform n=1000 (coordinate seed 1001), m=1000, cl=16, 2-opt of the "
+                                         "iteration best, alpha=1, beta=2, rho=0.02, p_best=0.01"),
     "clustered-n3800": dict(kind="clustered", n=3800, iseed=1003, m=1000, cl=16, ls=1, iters=500,
                             out="lstar_clustered_n3800.json",
                             text="clustered n=3800 (seed 1003), m=1000, cl=16, 2-opt of the iteration "
                                  "best, alpha=1, beta=2, rho=0.02, p_best=0.01"),
 }
+
+
+def instance(w):
+    """The coordinates of a single-colony workload."""
+    return I.uniform(w["n"], w["iseed"]) if w["kind"] == "uniform" else I.clustered(w["n"], w["iseed"])
 
 
 BATCH_SAMPLE = dict(count=256, size_seed=1000, lo=100, hi=2000, max_n=400, take=16, cl=32, iters=1000,
@@ -98,7 +110,7 @@ def main():
         return main_batch(args.iters or BATCH_SAMPLE["iters"], args.threads)
     w = WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
-    xy = I.uniform(w["n"], w["iseed"]) if w["kind"] == "uniform" else I.clustered(w["n"], w["iseed"])
+    xy = instance(w)
     runs = []
     for seed in (1, 2, 3):
         t0 = time.time()

@@ -21,6 +21,7 @@ import make_lstar  # noqa: E402
 
 # stored file -> (generator workload, benchmark workload)
 SINGLE = {"lstar_uniform_n1000.json": ("uniform-n1000", "uniform-n1000-cl32"),
+          "lstar_uniform_n1000_cl16_2opt.json": ("uniform-n1000-cl16-2opt", "learned-prior-n1000-cl16-2opt"),
           "lstar_clustered_n3800.json": ("clustered-n3800", "clustered-n3800-cl16-2opt")}
 
 
@@ -57,9 +58,11 @@ def test_single_colony_lstar(name):
     gen, wl = SINGLE[name]
     g, w = make_lstar.WORKLOADS[gen], bench.WORKLOADS[wl]
     # the benchmark's workload is the instance and colony the oracle ran
-    for key in ("n", "m", "cl", "iseed", "kind"):
+    for key in ("n", "m", "cl", "iseed"):
         assert g[key] == w[key], key
     assert g["ls"] == w.get("ls", 0)
+    xy = bench._instance(w)
+    assert np.array_equal(xy, make_lstar.instance(g))
     assert bench.LSTAR_FILES[wl][0] == name
     assert data["iterations"] == g["iters"]
     runs = data["runs"]
@@ -68,7 +71,6 @@ def test_single_colony_lstar(name):
     for r in runs:  # a global best never gets worse
         tr = r["trace_every_50"]
         assert all(a >= b for a, b in zip(tr, tr[1:])) and tr[-1] == r["best"]
-    xy = bench._instance(w)
     _check_bounds(xy, data["lstar"], g["ls"])
 
 
