@@ -42,3 +42,23 @@ def test_variant_matches_oracle(selection, tabu, n, m, iters):
         np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
     assert all(sorted(x) == list(range(n)) for x in t)
     g.close()
+
+
+def test_gpu_reservoir_runs_match_oracle_roulette_quality():
+    # whole runs of the GPU's reservoir selection and of the oracle's
+    # sequential roulette wheel both sample Eq. (1): over 20 seeds their final
+    # best lengths are one distribution (rank-sum test)
+    stats = pytest.importorskip("scipy.stats")
+    n, iters = 60, 40
+    xy = I.uniform(n, 4242)
+    gpu, orc = [], []
+    for seed in range(1, 21):
+        g = Colony(xy=xy, m=n, cl=0, rho=0.1, seed=seed)
+        g.iterate(iters)
+        gpu.append(g.best_tour()[0])
+        g.close()
+        o = O.Colony(xy=xy, m=n, cl=0, rho=0.1, seed=seed, selection=1, p_best=float(np.float32(0.01)))
+        o.iterate(iters, threads=1)
+        orc.append(int(o.best()[0]))
+    print(f"GPU reservoir mean {np.mean(gpu):.0f}, oracle roulette mean {np.mean(orc):.0f}")
+    assert stats.mannwhitneyu(gpu, orc).pvalue > 1e-3

@@ -86,3 +86,26 @@ def test_variant_tours_are_permutations_and_runs_improve(selection, tabu):
 def test_variants_need_whole_rows():
     with pytest.raises(ValueError, match="whole-row"):
         O.Colony(xy=I.uniform(20, 1), m=2, cl=8, selection=1)
+
+
+def _final_bests(n, iters, seeds, **kw):
+    xy = I.uniform(n, 4242)
+    out = []
+    for seed in seeds:
+        col = O.Colony(xy=xy, m=n, cl=0, rho=0.1, seed=seed, p_best=float(np.float32(0.01)), **kw)
+        col.iterate(iters, threads=1)
+        out.append(int(col.best()[0]))
+    return out
+
+
+def test_reservoir_and_roulette_runs_reach_the_same_quality():
+    # both selectors draw from Eq. (1), so whole runs of either are samples of
+    # one distribution of final lengths: a rank-sum test over 20 seeds finds no
+    # difference, while the same test separates a colony whose heuristic
+    # exponent is slightly off (beta = 1.5 for 2), so it has the power to see
+    # a wrong rule
+    wrs = _final_bests(60, 40, range(1, 21), selection=0)
+    rwm = _final_bests(60, 40, range(1, 21), selection=1)
+    assert scipy_stats.mannwhitneyu(wrs, rwm).pvalue > 1e-3
+    off = _final_bests(60, 40, range(1, 21), selection=0, beta=1.5)
+    assert scipy_stats.mannwhitneyu(wrs, off).pvalue < 1e-3
