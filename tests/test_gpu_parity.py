@@ -511,3 +511,21 @@ def test_two_opt_iteration_best_at_n18500_is_a_local_optimum():
 def test_two_opt_needs_candidate_lists():
     with pytest.raises(MMASError, match="ls needs"):
         Colony(xy=I.uniform(30, 1), cl=0, ls=1)
+
+
+def test_lattice_closed_form_bounds_every_gpu_tour():
+    # a 20 x 10 lattice with spacing 100 has an optimal tour of n * 100: no
+    # GPU tour is ever shorter, and a colony with 2-opt comes within 2% of it
+    # in 300 iterations (the oracle's colonies end 0.4-0.8% above it)
+    n = 200
+    xy = I.grid(20, 10, spacing=100)
+    g = Colony(xy=xy, m=n, cl=16, rho=0.1, seed=1, ls=1)
+    for _ in range(30):
+        g.iterate(10)
+        _, lens = g.tours()
+        assert lens.min() >= n * 100
+    best, tour = g.best_tour()
+    assert is_permutation(tour, n)
+    assert O.tour_length(O.distances(xy), tour) == best
+    assert n * 100 <= best <= 1.02 * n * 100, best
+    g.close()
