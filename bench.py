@@ -844,7 +844,7 @@ def run_ours_prior(args, w):
         target, target_source = 1.02 * lstar, f"1.02 L*, L* from tests/golden/{fname} (oracle, {how})"
     else:
         target = 1.02 * min(r["best_at_end"] for r in race.values())
-        target_source = "1.02 x the better final best of the two colonies (no oracle L* at this size)"
+        target_source = "1.02 x the best final length of the three colonies (no oracle L* at this size)"
     for r in race.values():
         r["seconds_to_target"] = next((t for t, b in r["trace"] if b <= target), None)
         r["trace"] = r["trace"][::max(1, len(r["trace"]) // 40)]
