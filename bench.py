@@ -292,7 +292,8 @@ def run_reference(args, w):
 
 
 def _cfg(w):
-    c = {"n": w["n"], "m": w["m"], "cl": w["cl"], "instance": f"{w['kind']} seed {w['iseed']}",
+    kind = "uniform" if w["kind"] == "prior" else w["kind"]  # the prior races on uniform instances
+    c = {"n": w["n"], "m": w["m"], "cl": w["cl"], "instance": f"{kind} seed {w['iseed']}",
          **PARAMS}
     if w.get("ls"):
         c["local_search"] = "2-opt of the iteration best" if w["ls"] == 1 else "2-opt of every ant"
