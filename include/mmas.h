@@ -144,6 +144,8 @@ typedef struct {
     int32_t construct_staged;  /* 1 if the choice table is staged in shared memory   */
     int32_t construct_smem;    /* dynamic shared memory per CTA, bytes               */
     int32_t row_pitch;         /* elements per row of the n x n device matrices      */
+    int64_t fallback_scans;    /* of the fallback steps, those that scanned the whole
+                                  row (the rest were decided on the reach list)      */
 } mmas_stats_t;
 
 /* Fill *p with the defaults listed at mmas_params (m = 0 means "m = n"). */

@@ -67,7 +67,8 @@ def lib():
                 "orc_word_row": (u32, [u64, i32, i32, i32, i32]),
                 "orc_word_slot": (u32, [u64, i32, i32, i32, i32]),
                 "orc_word_rwm": (u32, [u64, i32, i32, i32]),
-                "orc_rwm_rounds": (i32, [i32, P(f32), f32]),
+                "orc_variant_step": (i32, [vp, i32, i32, P(i32), i32, P(i32), P(f64), P(i32),
+                                           P(f64)]),
                 "orc_colony_set_variant": (None, [vp, i32, i32]),
                 "orc_start_node": (i32, [u64, i32, i32, i32]),
                 "orc_isqrt64": (u64, [u64]),
@@ -227,15 +228,10 @@ def wrs_pick(ids, w, r) -> int:
 
 
 def rwm_pick(w, u) -> int:
+    """The roulette wheel over weights w with draw u (orc_rwm_pick): the first
+    position whose cumulative sum exceeds u * sum(w); -1 if no weight is positive."""
     w = np.ascontiguousarray(w, dtype=np.float64)
     return lib().orc_rwm_pick(len(w), _f64p(w), float(u))
-
-
-def rwm_rounds(x, u) -> int:
-    """The exact single-precision parallel roulette wheel over weights x (see
-    orc_rwm_rounds); returns the winning position or -1."""
-    x = np.ascontiguousarray(x, dtype=np.float32)
-    return lib().orc_rwm_rounds(x.size, _f32p(x), float(np.float32(u)))
 
 
 def word_slot(seed, it, ant, t, j):
@@ -364,3 +360,20 @@ class Colony:
         mode = lib().orc_step_keys(self._h, it, ant, t, i,
                                    vis.ctypes.data_as(C.POINTER(C.c_uint8)), _f64p(keys))
         return mode, keys
+
+    def variant_step(self, it, ant, prefix, t):
+        """Step t of a whole-row variant replayed on prefix[0..t) (orc_variant_step).
+
+        Returns (pick, order, val, u): the oracle's node, the selectable
+        positions' nodes, what the selection compares at each position
+        (weights for the roulette wheel, keys for reservoir sampling) and the
+        roulette wheel's draw."""
+        pre = np.ascontiguousarray(prefix[:t], dtype=np.int32)
+        order = np.zeros(self.n, np.int32)
+        val = np.zeros(self.n, np.float64)
+        npos = C.c_int32()
+        u = C.c_double()
+        pick = lib().orc_variant_step(self._h, it, ant, _i32p(pre), t, _i32p(order), _f64p(val),
+                                      C.byref(npos), C.byref(u))
+        k = npos.value
+        return pick, order[:k], val[:k], u.value

@@ -331,77 +331,28 @@ ORC_API int32_t orc_wrs_pick(int32_t k, const int32_t *ids, const double *w, con
     return best;
 }
 
-/* Sequential roulette wheel (Sec. 4.2): walk the cumulative weights until they
- * exceed u * sum.  Used only to validate the statistical tests. */
+/* The roulette wheel (Sec. 4.2.1): node p of the k candidates is picked
+ * with probability w_p / sum(w), by drawing theta = u * T (u uniform in
+ * (0,1), T the sum of the weights) and walking the cumulative sums
+ * C(p) = w_0 + ... + w_p until one exceeds theta.  The sums are taken in
+ * double precision in position order; the winner is the first position
+ * whose cumulative sum exceeds theta (a position of weight 0 can never be
+ * that first one).  theta < T holds in double precision (u <= 1 - 2^-24), so
+ * a winner always exists when some weight is positive; -1 when none is. */
 ORC_API int32_t orc_rwm_pick(int32_t k, const double *w, double u)
 {
     double total = 0.0;
     for (int32_t i = 0; i < k; ++i) total += w[i];
-    double target = u * total, acc = 0.0;
+    if (!(total > 0.0)) return -1;
+    const double theta = u * total;
+    double acc = 0.0;
+    int32_t last = -1;
     for (int32_t i = 0; i < k; ++i) {
         acc += w[i];
-        if (target < acc) return i;
+        if (w[i] > 0.0) last = i;
+        if (theta < acc) return i;
     }
-    return k - 1;
-}
-
-/* The parallel roulette wheel (Sec. 4.2.1) as one exact single-precision
- * procedure, so that a 32-lane GPU implementation and this sequential one
- * pick the same position.  Weights x[0..N) (0 = not selectable) are taken in
- * rounds of 128 positions; in round r, lane l (0..31) owns positions
- * 128r + 4l .. 128r + 4l + 3 and forms its running partial sums
- * q0 = x0, q1 = q0 + x1, q2 = q1 + x2, q3 = q2 + x3; the lanes' totals q3 are
- * scanned inclusively (Hillis-Steele: for d = 1, 2, 4, 8, 16, S_l <- S_l +
- * S_{l-d} when l >= d); the rounds' totals S_31 accumulate into an offset O.
- * With the total T (the final O) and theta = u * T, the winner is the first
- * position p with x_p > 0 whose cumulative sum (O_r + S_{l-1}) + q_e exceeds
- * theta (S_{-1} = 0); if rounding leaves none, the last position with
- * x_p > 0.  Every operation is a float add or multiply rounded to nearest.
- * Returns -1 when no weight is positive. */
-static void rwm_round(const float *x, int32_t N, int32_t r, float q[32][4], float S[32])
-{
-    for (int l = 0; l < 32; ++l) {
-        float acc = 0.0f;
-        for (int e = 0; e < 4; ++e) {
-            const int32_t p = 128 * r + 4 * l + e;
-            const float v = p < N ? x[p] : 0.0f;
-            acc = e == 0 ? v : acc + v;
-            q[l][e] = acc;
-        }
-        S[l] = acc;
-    }
-    for (int d = 1; d < 32; d <<= 1) {
-        float T[32];
-        for (int l = 0; l < 32; ++l) T[l] = l >= d ? S[l] + S[l - d] : S[l];
-        memcpy(S, T, sizeof(T));
-    }
-}
-
-ORC_API int32_t orc_rwm_rounds(int32_t N, const float *x, float u)
-{
-    const int32_t rounds = (N + 127) / 128;
-    float q[32][4], S[32];
-    float total = 0.0f;
-    for (int32_t r = 0; r < rounds; ++r) {
-        rwm_round(x, N, r, q, S);
-        total = total + S[31];
-    }
-    const float theta = u * total;
-    float off = 0.0f;
-    for (int32_t r = 0; r < rounds; ++r) {
-        rwm_round(x, N, r, q, S);
-        for (int l = 0; l < 32; ++l) {
-            const float base = off + (l > 0 ? S[l - 1] : 0.0f);
-            for (int e = 0; e < 4; ++e) {
-                const int32_t p = 128 * r + 4 * l + e;
-                if (p < N && x[p] > 0.0f && base + q[l][e] > theta) return p;
-            }
-        }
-        off = off + S[31];
-    }
-    for (int32_t p = N - 1; p >= 0; --p)
-        if (x[p] > 0.0f) return p;
-    return -1;
+    return last;
 }
 
 ORC_API int64_t orc_two_opt(int32_t n, const int32_t *d, const int32_t *nn, int32_t k,
@@ -539,81 +490,120 @@ ORC_API void orc_colony_set_variant(orc_colony *c, int32_t sel, int32_t tabu)
     c->tabu = tabu;
 }
 
-/* A whole-row tour under the selected variant.  The compact list (Sec. 4.1):
- * entries[0..L) are the unvisited nodes; removing the node at slot j moves
- * the last one, t = entries[L-1], into slot j and records entries[t] = j
- * (when j < L-1), or marks entries[j] = n (when j = L-1); then L decreases.
- * Reservoir sampling over the list draws slot j's uniform from
- * orc_word_slot and keeps the largest log2(r)/w (ties -> lower node id);
- * over the bitmask it is the plain whole-row step.  The roulette wheel takes
- * the weights in list order (compact) or node order with visited nodes at
- * weight 0 (bitmask) and applies orc_rwm_rounds to the step's draw. */
+/* Remove node u from the compact list (Sec. 4.1): entries[0..L) are the
+ * unvisited nodes; an unvisited node u < L sits at its own index, otherwise
+ * entries[u] is the index it was moved to.  Its slot i_u is refilled by the
+ * list's last node t = entries[L-1], whose new index is recorded at
+ * entries[t]; when u is itself last, its slot takes the sentinel n. */
+static void ct_remove(int32_t *entries, int32_t *L, int32_t n, int32_t u)
+{
+    const int32_t iu = u < *L ? u : entries[u];
+    if (iu == *L - 1) {
+        entries[iu] = n;
+    } else {
+        const int32_t t = entries[*L - 1];
+        entries[iu] = t;
+        entries[t] = iu;
+    }
+    --*L;
+}
+
+/* Step t of a whole-row variant from node cur over the npos selectable
+ * positions, position p holding node order[p] (node order with visited nodes
+ * flagged in vis for the bitmask; list order for the compact list).  Fills
+ * val[p] with what the selection compares -- the weight choice_info (0 when
+ * visited) for the roulette wheel, the key log2(r)/w (NaN when visited) for
+ * reservoir sampling -- and returns the position picked:
+ *   roulette wheel: orc_rwm_pick with u from orc_word_rwm (one draw per step);
+ *   reservoir over the compact list: slot p's uniform from orc_word_slot,
+ *     largest key, ties -> lower node id;
+ *   reservoir over the bitmask: the plain whole-row keys of orc_step_keys. */
+static int32_t variant_select(const orc_colony *c, int32_t it, int32_t ant, int32_t t, int32_t cur,
+                              const int32_t *order, int32_t npos, const uint8_t *vis, double *val,
+                              double *u_out)
+{
+    const float *row = c->choice + (size_t)cur * c->n;
+    if (c->sel == 1) {
+        for (int32_t p = 0; p < npos; ++p)
+            val[p] = (vis && vis[order[p]]) ? 0.0 : (double)row[order[p]];
+        const double u = orc_uniform01(orc_word_rwm(c->seed, it, ant, t));
+        if (u_out) *u_out = u;
+        return orc_rwm_pick(npos, val, u);
+    }
+    if (!c->tabu) {
+        orc_step_keys(c, it, ant, t, cur, vis, val);
+        return argmax_keys(c->n, val);
+    }
+    int32_t best = -1;
+    for (int32_t p = 0; p < npos; ++p) {
+        const double r = orc_uniform01(orc_word_slot(c->seed, it, ant, t, p));
+        val[p] = log2(r) / (double)row[order[p]];
+        if (best < 0 || val[p] > val[best] || (val[p] == val[best] && order[p] < order[best]))
+            best = p;
+    }
+    return best;
+}
+
+/* A whole-row tour under the selected variant (cl = 0): the start node, then
+ * n - 1 selections by variant_select, the compact list updated by ct_remove
+ * or the bitmask by marking. */
 static int64_t construct_row_variant(const orc_colony *c, int32_t it, int32_t ant, int32_t *tour)
 {
     const int32_t n = c->n;
     uint8_t *vis = (uint8_t *)calloc((size_t)n, 1);
     int32_t *entries = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    float *x = (float *)malloc(sizeof(float) * (size_t)n);
-    double *keys = (double *)malloc(sizeof(double) * (size_t)n);
+    double *val = (double *)malloc(sizeof(double) * (size_t)n);
     for (int32_t v = 0; v < n; ++v) entries[v] = v;
     int32_t L = n;
     int32_t cur = orc_start_node(c->seed, it, ant, n);
     tour[0] = cur;
     vis[cur] = 1;
-    int32_t slot = cur;  /* the start node is at home */
-    for (int32_t t = 0; t < n; ++t) {
+    for (int32_t t = 1; t < n; ++t) {
+        int32_t next;
         if (c->tabu) {
-            /* remove `cur` from its slot */
-            if (slot == L - 1) {
-                entries[slot] = n;
-            } else {
-                const int32_t last = entries[L - 1];
-                entries[slot] = last;
-                entries[last] = slot;
-            }
-            --L;
-        }
-        if (t == n - 1) break;
-        const float *row = c->choice + (size_t)cur * n;
-        int32_t next = -1, nslot = -1;
-        if (c->sel == 0) {
-            if (c->tabu) {
-                double bk = 0.0;
-                for (int32_t j = 0; j < L; ++j) {
-                    const int32_t v = entries[j];
-                    const double r = orc_uniform01(orc_word_slot(c->seed, it, ant, t + 1, j));
-                    const double k = log2(r) / (double)row[v];
-                    if (next < 0 || k > bk || (k == bk && v < next)) {
-                        bk = k;
-                        next = v;
-                        nslot = j;
-                    }
-                }
-            } else {
-                orc_step_keys(c, it, ant, t + 1, cur, vis, keys);
-                next = argmax_keys(n, keys);
-            }
+            ct_remove(entries, &L, n, cur);
+            next = entries[variant_select(c, it, ant, t, cur, entries, L, NULL, val, NULL)];
         } else {
-            const float u = (float)orc_uniform01(orc_word_rwm(c->seed, it, ant, t + 1));
-            if (c->tabu) {
-                for (int32_t j = 0; j < L; ++j) x[j] = row[entries[j]];
-                nslot = orc_rwm_rounds(L, x, u);
-                next = entries[nslot];
-            } else {
-                for (int32_t v = 0; v < n; ++v) x[v] = vis[v] ? 0.0f : row[v];
-                next = orc_rwm_rounds(n, x, u);
-            }
+            next = variant_select(c, it, ant, t, cur, entries, n, vis, val, NULL);
         }
-        tour[t + 1] = next;
+        tour[t] = next;
         vis[next] = 1;
         cur = next;
-        slot = nslot;
     }
-    free(keys);
-    free(x);
+    free(val);
     free(entries);
     free(vis);
     return orc_tour_length(n, c->d, tour);
+}
+
+/* Step t of ant `ant` in iteration `it` replayed on a given prefix of t nodes
+ * (teacher forcing): rebuilds the tabu the prefix leaves (the compact list
+ * by removing prefix[0..t) in order, or the visited set), writes the
+ * selectable positions' nodes to order[], what the selection compares to
+ * val[] and their count to *npos, the roulette wheel's draw to *u_out, and
+ * returns the node the oracle picks.  Whole-row variants only. */
+ORC_API int32_t orc_variant_step(const orc_colony *c, int32_t it, int32_t ant, const int32_t *prefix,
+                                 int32_t t, int32_t *order, double *val, int32_t *npos, double *u_out)
+{
+    const int32_t n = c->n;
+    const int32_t cur = prefix[t - 1];
+    int32_t pick;
+    *u_out = 0.0;
+    if (c->tabu) {
+        int32_t L = n;
+        for (int32_t v = 0; v < n; ++v) order[v] = v;
+        for (int32_t j = 0; j < t; ++j) ct_remove(order, &L, n, prefix[j]);
+        *npos = L;
+        pick = order[variant_select(c, it, ant, t, cur, order, L, NULL, val, u_out)];
+    } else {
+        uint8_t *vis = (uint8_t *)calloc((size_t)n, 1);
+        for (int32_t j = 0; j < t; ++j) vis[prefix[j]] = 1;
+        for (int32_t v = 0; v < n; ++v) order[v] = v;
+        *npos = n;
+        pick = variant_select(c, it, ant, t, cur, order, n, vis, val, u_out);
+        free(vis);
+    }
+    return pick;
 }
 
 /* One ant's tour in iteration `it` (Alg. 1, inner loops): a random start, then

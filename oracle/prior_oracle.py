@@ -92,38 +92,73 @@ def _mean_nbr32(h, nn):
     return (acc * np.float32(1.0 / K_NN)).astype(np.float32)
 
 
+def _rounding(gpu_rounding):
+    return bf16 if gpu_rounding else (lambda x: np.asarray(x, np.float64))
+
+
+def _lin(x, W, b, r):
+    """x W^T (+ b): the exact product (fp64) of the operands after rounding r."""
+    y = r(x).astype(np.float64) @ r(W).astype(np.float64).T
+    if b is not None:
+        y = y + np.asarray(b, np.float64)
+    return y
+
+
+def input_layer(F, W0, b0, gpu_rounding):
+    """h0 = relu(F0 W0^T + b0): fp32 after bf16 operands, else fp64."""
+    f = np.float32 if gpu_rounding else np.float64
+    return np.maximum(_lin(F, W0, b0, _rounding(gpu_rounding)), 0.0).astype(f)
+
+
+def mp_layer(h, nn, W, b, gpu_rounding):
+    """One message-passing layer: m_i = mean_k h[nn[i][k]], z = [h | m],
+    h' = relu(z W^T + b) + h.  Rounded: the mean of the bf16 h summed in fp32
+    over k = 0..15 in order, z in bf16, h' stored in fp32.  Returns (h', z, pre)."""
+    r = _rounding(gpu_rounding)
+    if gpu_rounding:
+        m = _mean_nbr32(r(h), nn)
+    else:
+        m = np.asarray(h, np.float64)[nn].mean(axis=1)
+    z = np.concatenate([r(h), r(m)], axis=1)
+    pre = _lin(z, W, b, r)
+    f = np.float32 if gpu_rounding else np.float64
+    return (np.maximum(pre, 0.0) + h).astype(f), z, pre
+
+
+def query(h, Wq, gpu_rounding):
+    """q = h Wq^T (fp32 after bf16 operands, else fp64)."""
+    f = np.float32 if gpu_rounding else np.float64
+    return _lin(h, Wq, None, _rounding(gpu_rounding)).astype(f)
+
+
+def edge_scores(q, h, nn, dn, a, c, gpu_rounding):
+    """s[i][k] = <q_i, h[nn[i][k]]> / 8 + a dn[i][k] + c.  Rounded: h in bf16,
+    the dot summed in fp32 over c = 0..63 in order, a and c in fp32."""
+    if gpu_rounding:
+        hb = bf16(h)
+        dot = np.zeros(nn.shape, np.float32)
+        for ch in range(H):  # float32, c = 0..63 in order
+            dot = (dot + q[:, ch][:, None] * hb[nn, ch]).astype(np.float32)
+        return (dot * np.float32(0.125) + np.float32(a) * dn + np.float32(c)).astype(np.float32)
+    q = np.asarray(q, np.float64)
+    h = np.asarray(h, np.float64)
+    return np.einsum("ic,ikc->ik", q, h[nn]) / 8.0 + a * np.asarray(dn, np.float64) + c
+
+
 def forward(params, F, dn, nn, gpu_rounding=True):
-    """Scores s [n][16] (float32 when gpu_rounding, else float64) and the cache."""
+    """Scores s [n][16] (float32 when gpu_rounding, else float64) and the cache.
+    The same stages in both modes; only their rounding differs."""
     p = unpack(params)
     nn = np.asarray(nn, np.int64)
-    r = bf16 if gpu_rounding else (lambda x: np.asarray(x, np.float64))
-    f = np.float32 if gpu_rounding else np.float64
-
-    def lin(x, W, b=None):  # exact product of the (rounded) operands
-        y = r(x).astype(np.float64) @ r(W).astype(np.float64).T
-        if b is not None:
-            y = y + np.asarray(b, np.float64)
-        return y
-
     cache = {"F": F, "dn": dn, "nn": nn}
-    h = np.maximum(lin(F, p["W0"], p["b0"]), 0.0).astype(f)
+    h = input_layer(F, p["W0"], p["b0"], gpu_rounding)
     cache["h0"] = h
     for l in (1, 2, 3):
-        m = _mean_nbr32(r(h), nn) if gpu_rounding else h[nn].mean(axis=1)
-        z = np.concatenate([r(h), r(m)], axis=1) if gpu_rounding else np.concatenate([h, m], axis=1)
-        pre = lin(z, p[f"W{l}"], p[f"b{l}"])
-        h = (np.maximum(pre, 0.0) + h).astype(f)
+        h, z, pre = mp_layer(h, nn, p[f"W{l}"], p[f"b{l}"], gpu_rounding)
         cache[f"z{l}"], cache[f"pre{l}"], cache[f"h{l}"] = z, pre, h
-    q = lin(h, p["Wq"]).astype(f)
-    hb = r(h)
-    if gpu_rounding:
-        dot = np.zeros(nn.shape, np.float32)
-        for c in range(H):  # float32, c = 0..63 in order
-            dot = (dot + q[:, c][:, None] * hb[nn, c]).astype(np.float32)
-        s = (dot * np.float32(0.125) + np.float32(p["a"][0]) * dn + np.float32(p["c"][0])).astype(np.float32)
-    else:
-        s = np.einsum("ic,ikc->ik", q, h[nn]) / 8.0 + p["a"][0] * dn + p["c"][0]
+    q = query(h, p["Wq"], gpu_rounding)
     cache["q"] = q
+    s = edge_scores(q, h, nn, dn, p["a"][0], p["c"][0], gpu_rounding)
     return s, cache
 
 

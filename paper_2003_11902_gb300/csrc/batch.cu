@@ -123,8 +123,10 @@ __global__ void k_batch_gather(Scalars *const *scs, int count, int32_t *best,
 
 __global__ void k_batch_reset_fallbacks(Scalars *const *scs, int count)
 {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x)
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
         scs[b]->fallback_steps = 0;
+        scs[b]->fallback_scans = 0;
+    }
 }
 
 void free_batch(mmas_batch *b)

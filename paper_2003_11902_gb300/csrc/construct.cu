@@ -212,6 +212,9 @@ __device__ __forceinline__ int greedy_reach(const uint2 *__restrict__ xl, const 
     return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
 }
 
+// Bit set in a fallback's result when the whole row was scanned.
+constexpr int FB_SCANNED = 1 << 30;
+
 // Candidate-list fallback, out of line so the hot step stays compact:
 // fallback = 0 takes the unvisited node of largest choice_info (ties -> lower
 // id), first from cur's reach list when that decides it, else from the row;
@@ -233,9 +236,18 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
             const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane);
             if (r >= 0) return r;
         }
-        return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
+        return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
     }
-    return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur);
+    return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
+}
+
+// Count one fallback step in fbn's low half and, when its row was scanned
+// (FB_SCANNED set in the fallback's result), one row scan in its high half;
+// return the picked node.
+__device__ __forceinline__ int count_fallback(int r, unsigned long long &fbn)
+{
+    fbn += 1ull + ((unsigned long long)((unsigned)r >> 30) << 32);
+    return r & (FB_SCANNED - 1);
 }
 
 // Slot `idx` (row cur) of the candidate table: cc / cw are the staged (or
@@ -260,7 +272,7 @@ template <int TW, bool PART>
 __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t *cc,
                                          const float *cw, const Tabu<TW> &tb, int lane,
                                          int cur, float lg, int t, int ant, uint32_t it,
-                                         uint32_t &fbn)
+                                         unsigned long long &fbn)
 {
     const bool act = lane < a.cl;
     uint32_t v = 0;
@@ -271,11 +283,11 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     const uint32_t k = ok ? neg_key(__fmul_rn(lg, wi)) : 0u;
     const uint32_t mx = __reduce_max_sync(FULL, k);
     if (__builtin_expect(mx != 0u, 1)) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
-    ++fbn;
-    return cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
-                             (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
-                             a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                             a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe);
+    return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
+                                            (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
+                                            cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+                          fbn);
 }
 
 // Store the window of steps [32w, t_end]: lane l holds entry 32w + l.
@@ -292,7 +304,7 @@ template <bool CHECK, int TW, bool PART>
 __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_t *cc,
                                            const float *cw, Tabu<TW> &tb, int32_t *trow,
                                            int lane, int ant, uint32_t it, int g, float (&lg)[4],
-                                           int &cur, int &twin, uint32_t &fbn)
+                                           int &cur, int &twin, unsigned long long &fbn)
 {
     uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
     float nl[4];
@@ -334,7 +346,7 @@ template <int TW, bool PART, bool CL32>
 __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const uint16_t *cc,
                                                 const float *cw, Tabu<TW> &tb, int lane,
                                                 int ant, uint32_t it, int g, float (&lg)[4],
-                                                int &cur, int &twin, uint32_t &fbn)
+                                                int &cur, int &twin, unsigned long long &fbn)
 {
     uint4 nx = make_uint4((uint32_t)lane, (uint32_t)(g + 1), (uint32_t)ant, it);
     float nl[4];
@@ -373,12 +385,13 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
     }
     if (__builtin_expect(jfail < 4, 0)) {
         // step 4g + jfail: every candidate of cur is visited
-        ++fbn;
         const int t = 4 * g + jfail;
-        const int fb = cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
-                                         (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
-                                         cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                         a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe);
+        const int fb = count_fallback(
+            cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
+                              (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
+                              a.xlw + (size_t)cur * a.xe, a.xlb + cur,
+                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+            fbn);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
         cur = fb;
@@ -489,7 +502,7 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
     tb.mark(lane, start);
     int cur = start;
     int twin = start;  // lane l holds entry 32w + l of the current window
-    uint32_t fbn = 0;
+    unsigned long long fbn = 0;
 
     if constexpr (MODE == CAND) {
         float lg[4];
@@ -531,7 +544,10 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
             cur = next;
         }
     }
-    if (lane == 0 && fbn) atomicAdd(&a.sc->fallback_steps, (unsigned long long)fbn);
+    if (lane == 0 && fbn) {
+        atomicAdd(&a.sc->fallback_steps, fbn & 0xFFFFFFFFull);
+        if (fbn >> 32) atomicAdd(&a.sc->fallback_scans, fbn >> 32);
+    }
 }
 
 // Stage `bytes_w` bytes of weights and `bytes_c` of ids into shared memory

@@ -32,6 +32,7 @@ struct Scalars {
     uint32_t err;          // ERR_* bits
     uint32_t done;         // CTAs of the scoring kernel that finished (last-block election)
     unsigned long long fallback_steps;  // cumulative candidate-list fallbacks
+    unsigned long long fallback_scans;  // of those, the ones that scanned the whole row
     long long nn_len;      // nearest-neighbour tour length
     long long iterations;  // completed iterations
 };

@@ -595,6 +595,7 @@ mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out)
     out->construct_staged = h->cplan.staged;
     out->construct_smem = (int32_t)h->cplan.smem;
     out->row_pitch = h->ld;
+    out->fallback_scans = (int64_t)s.fallback_scans;
     return MMAS_OK;
 }
 

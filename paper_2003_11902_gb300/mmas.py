@@ -61,7 +61,8 @@ class mmas_stats_t(C.Structure):
                 ("best_len", C.c_int32), ("iter_best_len", C.c_int32), ("tau_min", C.c_float),
                 ("tau_max", C.c_float), ("construct_grid", C.c_int32),
                 ("construct_block", C.c_int32), ("construct_staged", C.c_int32),
-                ("construct_smem", C.c_int32), ("row_pitch", C.c_int32)]
+                ("construct_smem", C.c_int32), ("row_pitch", C.c_int32),
+                ("fallback_scans", C.c_int64)]
 
 
 class MMASError(RuntimeError):

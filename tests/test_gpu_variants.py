@@ -1,13 +1,16 @@
 """Whole-row variants on the GPU (Sec. 4.1 compact tabu, Sec. 4.2.1 roulette
-wheel) against the oracle: tours, lengths, best tour and pheromone equal,
-iteration by iteration (the roulette wheel is an exact single-precision
-procedure on both sides; the reservoir keys over the compact list are
-compared as the bitmask ones are, near-ties aside)."""
+wheel) against the oracle, iteration by iteration in lockstep: every step of
+every GPU tour is replayed by the oracle on the GPU's prefix (teacher forcing,
+tests/parity.py).  Roulette picks may differ only where the draw lies within
+the single-precision rounding bound of an interval boundary, reservoir picks
+only at near-ties; lengths are bit-exact and the pheromone agrees within
+1e-5 relative after the oracle applies the GPU's iteration best."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2003_11902_gb300 import Colony, instances as I
+from parity import check_ant_variant
 
 pytestmark = pytest.mark.gpu
 
@@ -25,22 +28,22 @@ def test_variant_matches_oracle(selection, tabu, n, m, iters):
     kw = dict(m=m, cl=0, rho=0.1, seed=5, selection=selection, tabu=tabu)
     g = Colony(xy=xy, **kw)
     o = O.Colony(xy=xy, p_best=float(np.float32(0.01)), **kw)
+    d = o.state()["d"]
+    counts = {"steps": 0, "boundary": 0, "near_tie": 0}
     for it in range(iters):
         g.iterate(1)
-        o.iterate(1)
         t, lens = g.tours()
-        ot, ol, _ = o.tours()
-        same = [np.array_equal(t[k], ot[k]) for k in range(m)]
-        assert np.array_equal(lens[same], ol[same])
-        if selection == 1:
-            assert all(same), f"iteration {it}: roulette tours differ for ants {np.flatnonzero(~np.array(same))}"
-        else:
-            assert sum(same) >= m - max(1, m // 10), "reservoir tours differ beyond near-ties"
-        if not all(same):
-            break  # a near-tie changed the pheromone: later iterations diverge legitimately
+        for k in range(m):
+            check_ant_variant(o, it, k, t[k], counts)
+            assert lens[k] == O.tour_length(d, t[k]), f"ant {k}: length"
+        ib = int(np.argmin(lens))  # ties -> lower ant
+        o.update(t[ib], int(lens[ib]))
         tau, tmin, tmax = g.pheromone()
+        assert (tmin, tmax) == o.limits()
         np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
-    assert all(sorted(x) == list(range(n)) for x in t)
+    print(f"selection {selection} tabu {tabu} n {n}: {counts['steps']} steps, "
+          f"{counts['boundary']} near-boundary and {counts['near_tie']} near-tie divergences")
+    assert counts["boundary"] + counts["near_tie"] <= counts["steps"] // 1000 + 1
     g.close()
 
 

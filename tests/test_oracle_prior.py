@@ -102,3 +102,142 @@ def test_labels_mark_tour_edges_both_ways():
         for k in range(P.K_NN):
             j = int(nn[i, k])
             assert y[i, k] == (succ[i] == j or succ[j] == i)
+
+
+# ---------------------------------------------------------------------------
+# The forward pass at the GPU's rounding points, pinned to the unrounded one.
+#
+# forward() chains four stages (input layer, three message-passing layers, the
+# query, the edge scores), the same in both modes.  Each stage is checked on its
+# own: fed the SAME input (the rounded pass's own activations), its rounded form
+# (bf16 GEMM operands, unit roundoff 2^-8; fp32 storage and fp32 sums, unit
+# roundoff 2^-24) must lie element by element within a bound on that stage's
+# rounding alone from its unrounded form.  For a product with rounded operands,
+# A'B' - AB = (A' - A)B' + A(B' - B), so |A'B' - AB| <= |A' - A||B'| + |A||B' - B|;
+# relu and the residual add are 1-Lipschitz; an fp32 sum of k terms is off by at
+# most k 2^-24 times the sum of their magnitudes, and each fp32 store by 2^-24 of
+# the value stored.  A mistake confined to the rounded path (a swapped half of z,
+# a dropped term, a wrong neighbour) moves a stage by O(1) and breaks its bound.
+
+UF = 2.0 ** -24
+SLACK = 1 + 1e-6
+
+
+def _b64(x):
+    return P.bf16(np.asarray(x, np.float32)).astype(np.float64)
+
+
+def _abs_err_of_product(x, W):
+    """|bf16(x) bf16(W)^T - x W^T| bound, element by element."""
+    x = np.asarray(x, np.float64)
+    W = np.asarray(W, np.float64)
+    return np.abs(_b64(x) - x) @ np.abs(_b64(W)).T + np.abs(x) @ np.abs(_b64(W) - W).T
+
+
+def _mp_bound(x, nn, W, hr):
+    """Bound on |rounded - unrounded| of one message-passing layer on input x."""
+    x64 = np.asarray(x, np.float64)
+    xb = _b64(x)
+    m32 = P._mean_nbr32(P.bf16(x), nn).astype(np.float64)     # the fp32 mean of bf16 h
+    m_exact = x64[nn].mean(axis=1)
+    # |m32 - m| <= mean |bf16(h) - h| + the fp32 sum's rounding
+    Em = np.abs(xb - x64)[nn].mean(axis=1) + P.K_NN * UF * np.abs(xb[nn]).mean(axis=1)
+    Ez = np.concatenate([np.abs(xb - x64), np.abs(_b64(m32) - m32) + Em], axis=1)
+    W = np.asarray(W, np.float64)
+    Epre = Ez @ np.abs(_b64(W)).T + np.abs(np.concatenate([x64, m_exact], axis=1)) @ np.abs(_b64(W) - W).T
+    return (Epre + UF * np.abs(hr)) * SLACK
+
+
+def _check_stages(params, F, dn, nn):
+    p = P.unpack(np.asarray(params, np.float64))
+    nn = np.asarray(nn, np.int64)
+    _, cr = P.forward(params, F, dn, nn, gpu_rounding=True)
+    worst = []
+    # input layer on F
+    hr = P.input_layer(F, p["W0"], p["b0"], True)
+    he = P.input_layer(F, p["W0"], p["b0"], False)
+    bound = (_abs_err_of_product(F, p["W0"]) + UF * np.abs(hr)) * SLACK
+    worst.append(np.max(np.abs(hr - he) / bound))
+    assert np.array_equal(hr, cr["h0"])
+    # message-passing layers, each on the rounded pass's own input
+    for l in (1, 2, 3):
+        x = cr[f"h{l - 1}"]
+        hr, zr, _ = P.mp_layer(x, nn, p[f"W{l}"], p[f"b{l}"], True)
+        he, ze, _ = P.mp_layer(x, nn, p[f"W{l}"], p[f"b{l}"], False)
+        assert np.array_equal(hr, cr[f"h{l}"])
+        worst.append(np.max(np.abs(hr - he) / _mp_bound(x, nn, p[f"W{l}"], hr)))
+        assert np.array_equal(zr[:, :P.H], P.bf16(x))              # z = [h | m] in that order
+    # query on h3
+    x = cr["h3"]
+    qr = P.query(x, p["Wq"], True)
+    qe = P.query(x, p["Wq"], False)
+    assert np.array_equal(qr, cr["q"])
+    bound = (_abs_err_of_product(x, p["Wq"]) + UF * np.abs(qr)) * SLACK
+    worst.append(np.max(np.abs(qr - qe) / bound))
+    # edge scores on (q, h3): bf16 h, fp32 products and sums (two roundings a
+    # term), fp32 a and c and three fp32 operations at the end
+    a, c = p["a"][0], p["c"][0]
+    sr = P.edge_scores(qr, x, nn, dn, a, c, True)
+    se = P.edge_scores(qr, x, nn, dn, a, c, False)
+    q64 = np.asarray(qr, np.float64)
+    x64 = np.asarray(x, np.float64)
+    xb = _b64(x)
+    dn64 = np.asarray(dn, np.float64)
+    a32, c32 = float(np.float32(a)), float(np.float32(c))
+    Edot = (np.einsum("ic,ikc->ik", np.abs(q64), np.abs(xb - x64)[nn])
+            + 2 * P.H * UF * np.einsum("ic,ikc->ik", np.abs(q64), np.abs(xb[nn])))
+    dot = np.einsum("ic,ikc->ik", q64, xb[nn])
+    bound = (Edot / 8 + abs(a - a32) * dn64 + abs(c - c32)
+             + 4 * UF * (np.abs(dot) / 8 + abs(a32) * dn64 + abs(c32))) * SLACK + 1e-30
+    worst.append(np.max(np.abs(sr.astype(np.float64) - se) / bound))
+    return worst
+
+
+def _prior_case(n, seed):
+    xy, d, nn = _graph(n, seed)
+    F, dn = P.features(xy, d, nn)
+    params = I.prior_params(seed).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    q = P.unpack(params)
+    for name in ("b0", "b1", "b2", "b3"):
+        q[name][:] = rng.normal(0, 0.2, q[name].shape)
+    q["c"][0] = 0.3
+    return P.pack(q).astype(np.float32).astype(np.float64), F, dn, nn
+
+
+@pytest.mark.parametrize("n,seed", [(60, 21), (400, 22)])
+def test_rounded_forward_stages_within_their_rounding_bounds(n, seed):
+    params, F, dn, nn = _prior_case(n, seed)
+    worst = _check_stages(params, F, dn, nn)
+    print("worst error / bound per stage:", [f"{w:.3f}" for w in worst])
+    assert all(w <= 1.0 for w in worst)
+    assert all(w > 0 for w in worst)  # every stage really rounds
+
+
+def test_rounded_stage_bound_catches_a_swapped_message():
+    # a planted mistake in the rounded pass only: the layer computed with z =
+    # [m | h] (equivalently, the halves of W_l exchanged) leaves the stage's
+    # bound for a good share of the elements (the rest sit where relu cuts the
+    # layer off in both), while the correct rounded layer stays inside it
+    params, F, dn, nn = _prior_case(200, 23)
+    nn = np.asarray(nn, np.int64)
+    p = P.unpack(params)
+    _, cr = P.forward(params, F, dn, nn, gpu_rounding=True)
+    x = cr["h1"]
+    W = p["W2"]
+    Wswap = np.concatenate([W[:, P.H:], W[:, :P.H]], axis=1)
+    he, _, _ = P.mp_layer(x, nn, W, p["b2"], False)
+    good, _, _ = P.mp_layer(x, nn, W, p["b2"], True)
+    bad, _, _ = P.mp_layer(x, nn, Wswap, p["b2"], True)
+    assert np.all(np.abs(good - he) <= _mp_bound(x, nn, W, good))
+    ratio = np.abs(bad - he) / _mp_bound(x, nn, W, bad)
+    assert np.mean(ratio > 1) > 0.2 and ratio.max() > 10
+
+
+def test_whole_rounded_forward_stays_near_the_unrounded_one():
+    # end to end, the rounding of four stages moves each score by well under
+    # one percent of the score range (observed on this case: ~0.3%)
+    params, F, dn, nn = _prior_case(400, 24)
+    sr, _ = P.forward(params, F, dn, nn, gpu_rounding=True)
+    se, _ = P.forward(params, F, dn, nn, gpu_rounding=False)
+    assert np.max(np.abs(sr - se)) < 1e-2 * (np.abs(se).max() + 1)

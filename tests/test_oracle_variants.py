@@ -11,7 +11,10 @@ from paper_2003_11902_gb300 import instances as I
 scipy_stats = pytest.importorskip("scipy.stats")
 
 
-def test_roulette_pick_is_exact_up_to_float_rounding():
+def test_roulette_pick_matches_exact_cumulative_sums():
+    # the pick p satisfies C(p-1) <= u T < C(p) for the exact rational sums
+    # C(p) = w_0 + ... + w_p and T = C(N-1), up to the double rounding of the
+    # oracle's own running sums (N 2^-52 T), and its weight is positive
     rng = np.random.default_rng(0)
     for trial in range(300):
         N = int(rng.integers(1, 700))
@@ -19,16 +22,24 @@ def test_roulette_pick_is_exact_up_to_float_rounding():
         x[rng.random(N) < 0.3] = 0.0
         if not (x > 0).any():
             x[int(rng.integers(0, N))] = 1.0
-        u = np.float32((int(rng.integers(0, 1 << 23)) + 0.5) / (1 << 23))
-        p = O.rwm_rounds(x, u)
+        u = (int(rng.integers(0, 1 << 23)) + 0.5) / (1 << 23)
+        p = O.rwm_pick(x.astype(np.float64), u)
         assert p >= 0 and x[p] > 0
-        # exact cumulative sums: C(p-1) <= u T < C(p), up to 1e-5 relative (float sums)
         fx = [Fraction(float(v)) for v in x]
         T = sum(fx)
         below = sum(fx[:p])
-        theta = Fraction(float(u)) * T
-        tol = T * Fraction(1, 100000)
-        assert below - tol <= theta <= below + fx[p] + tol
+        theta = Fraction(u) * T
+        tol = T * N * Fraction(1, 2 ** 52)
+        assert below - tol <= theta < below + fx[p] + tol
+
+
+def test_roulette_pick_edge_cases():
+    assert O.rwm_pick(np.zeros(5), 0.5) == -1                  # nothing selectable
+    assert O.rwm_pick(np.array([0.0, 0.0, 3.0, 0.0]), 1 - 2.0 ** -24) == 2   # the only positive weight
+    # theta = u T = 2 lands exactly on C(0) = 2: the first sum that EXCEEDS theta wins
+    assert O.rwm_pick(np.array([2.0, 2.0]), 0.5) == 1
+    assert O.rwm_pick(np.array([2.0, 0.0, 2.0]), 0.5) == 2      # a zero weight never wins
+    assert O.rwm_pick(np.array([2.0, 2.0]), 0.5 - 2.0 ** -30) == 0
 
 
 def test_roulette_frequencies_follow_the_weights():
@@ -37,13 +48,52 @@ def test_roulette_frequencies_follow_the_weights():
     x[rng.choice(300, 20, replace=False)] = rng.uniform(0.5, 2.0, 20)
     counts = np.zeros(300)
     for k in range(40000):
-        u = np.float32((O.word_rwm(7, k, 0, 1) >> 9) * 2.0 ** -23 + 2.0 ** -24)
-        counts[O.rwm_rounds(x, u)] += 1
+        u = O.uniform01(O.word_rwm(7, k, 0, 1))
+        counts[O.rwm_pick(x.astype(np.float64), u)] += 1
     sel = x > 0
     assert counts[~sel].sum() == 0
     xs = x[sel].astype(np.float64)
     exp = counts.sum() * xs / xs.sum()
     assert scipy_stats.chisquare(counts[sel], exp).pvalue > 1e-3
+
+
+def test_compact_list_worked_example():
+    # Sec. 4.1's rule applied by hand to nodes 0..7, removing 2, 5 and 7:
+    #   remove 2 (at home): the last node 7 takes slot 2, entries[7] = 2
+    #       -> [0 1 7 3 4 5 6 | 2]
+    #   remove 5 (at home): the last node 6 takes slot 5, entries[6] = 5
+    #       -> [0 1 7 3 4 6 | 5 2]
+    #   remove 7 (moved, entries[7] = 2): the last node 6 takes slot 2,
+    #       entries[6] = 2 -> [0 1 6 3 4 | 6 2 2]
+    col = O.Colony(xy=I.uniform(8, 3), m=1, cl=0, rho=0.1, seed=1, selection=1, tabu=1)
+    _, order, _, _ = col.variant_step(0, 0, np.array([2, 5, 7], np.int32), 3)
+    assert list(order) == [0, 1, 6, 3, 4]
+
+
+@pytest.mark.parametrize("n", [9, 64, 300])
+def test_compact_list_holds_exactly_the_unvisited_nodes(n):
+    # after any prefix of removals the left part is exactly the unvisited set
+    # and an unvisited node below L sits at its own index (Sec. 4.1's invariant)
+    col = O.Colony(xy=I.uniform(n, 11), m=1, cl=0, rho=0.1, seed=2, selection=1, tabu=1)
+    perm = I.random_permutation(n, 5)
+    for t in range(1, n):
+        pick, order, val, u = col.variant_step(0, 0, perm, t)
+        assert sorted(order) == sorted(set(range(n)) - set(perm[:t].tolist()))
+        L = len(order)
+        for j, v in enumerate(order):
+            assert (v == j) if v < L else True
+        assert pick in set(order.tolist())
+
+
+@pytest.mark.parametrize("selection,tabu", [(0, 1), (1, 0), (1, 1)])
+def test_variant_replay_reproduces_the_oracle_tours(selection, tabu):
+    # teacher forcing on the oracle's own tours picks every node again
+    n = 50
+    col = O.Colony(xy=I.uniform(n, 21), m=4, cl=0, rho=0.1, seed=6, selection=selection, tabu=tabu)
+    for ant in range(4):
+        _, tour, _ = col.construct(0, ant)
+        for t in range(1, n):
+            assert col.variant_step(0, ant, tour, t)[0] == tour[t]
 
 
 @pytest.mark.parametrize("selection,tabu", [(0, 1), (1, 0), (1, 1)])
