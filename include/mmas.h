@@ -287,9 +287,23 @@ mmas_status mmas_prior_create(const float *params, int32_t device, mmas_prior **
 /* Replace the parameters (and reset the optimiser state). */
 mmas_status mmas_prior_set_params(mmas_prior *p, const float *params);
 mmas_status mmas_prior_get_params(mmas_prior *p, float *params);
+/* The optimiser's state, for checkpoints and for checking a training step:
+ * Adam's first and second moments m and v (host, MMAS_PRIOR_PARAMS floats
+ * each), the gradient computed by the last mmas_prior_train step or
+ * mmas_prior_grad call (host, MMAS_PRIOR_PARAMS floats; zeros before any), and
+ * the number of Adam steps taken (*step).  Any pointer may be NULL.
+ * Synchronises the device. */
+mmas_status mmas_prior_get_state(mmas_prior *p, float *m, float *v, float *grad, int32_t *step);
+/* Restore Adam's moments (finite, v >= 0) and step count, e.g. from a
+ * checkpoint written with mmas_prior_get_state.  Errors: EINVAL. */
+mmas_status mmas_prior_set_state(mmas_prior *p, const float *m, const float *v, int32_t step);
 /* Scores s [n][16] (host, row-major) of colony h's candidate edges. */
 mmas_status mmas_prior_scores(mmas_prior *p, mmas_handle *h, float *scores);
-/* `steps` Adam steps (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the mean binary
+/* `steps` Adam steps (Kingma and Ba, "Adam: a method for stochastic
+ * optimization", ICLR 2015; lr; beta1 0.9, beta2 0.999, eps 1e-8, each a
+ * single-precision value; per parameter m <- b1 m + (1 - b1) g,
+ * v <- b2 v + (1 - b2) g^2, theta <- theta - lr (m / c1) / (sqrt(v / c2) + eps)
+ * with c1 = 1 - b1^t, c2 = 1 - b2^t for step number t) on the mean binary
  * cross-entropy of sigmoid(s) against y[i][k] = [(i, nn[i][k]) is an edge of
  * `tour`] (host, a permutation of 0..n-1); *loss (may be NULL) = the loss of
  * the last step's forward pass. */

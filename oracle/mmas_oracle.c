@@ -199,28 +199,28 @@ ORC_API void orc_eta_beta(int32_t n, const int32_t *d, double beta, float *eb)
 }
 
 /* Candidate lists (Sec. 4.3): for each node, the cl closest other nodes in
- * ascending (distance, id) order.  cand is n x cl. */
-static const int32_t *g_cmp_row;
-static int cmp_by_dist_then_id(const void *a, const void *b)
-{
-    int32_t ia = *(const int32_t *)a, ib = *(const int32_t *)b;
-    int32_t da = g_cmp_row[ia], db = g_cmp_row[ib];
-    if (da != db) return da < db ? -1 : 1;
-    return ia < ib ? -1 : (ia > ib ? 1 : 0);
-}
-
+ * ascending (distance, id) order.  cand is n x cl.  Each row is one pass over
+ * the other nodes j in increasing id, keeping the cl smallest (d, id) pairs
+ * seen so far in order: a node enters when its distance is strictly smaller
+ * than the last kept one's (an equal distance loses to the lower id already
+ * kept), displacing the last. */
 ORC_API void orc_candidates(int32_t n, const int32_t *d, int32_t cl, int32_t *cand)
 {
-    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     for (int32_t i = 0; i < n; ++i) {
-        int32_t k = 0;
-        for (int32_t j = 0; j < n; ++j)
-            if (j != i) idx[k++] = j;
-        g_cmp_row = d + (size_t)i * n;
-        qsort(idx, (size_t)k, sizeof(int32_t), cmp_by_dist_then_id);
-        for (int32_t c = 0; c < cl; ++c) cand[(size_t)i * cl + c] = idx[c];
+        const int32_t *row = d + (size_t)i * n;
+        int32_t *best = cand + (size_t)i * cl;
+        int32_t k = 0;  /* entries kept so far */
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (k == cl && row[j] >= row[best[cl - 1]]) continue;
+            int32_t p = k < cl ? k++ : cl - 1;  /* the slot j takes before moving up */
+            while (p > 0 && row[best[p - 1]] > row[j]) {
+                best[p] = best[p - 1];
+                --p;
+            }
+            best[p] = j;
+        }
     }
-    free(idx);
 }
 
 /* Tour length: sum of d over consecutive nodes, closing the cycle. */

@@ -202,6 +202,23 @@ def backward(params, cache, y):
     return pack(g)
 
 
+# Adam's hyperparameters as the library holds them: single-precision values
+ADAM_B1, ADAM_B2, ADAM_EPS = float(np.float32(0.9)), float(np.float32(0.999)), float(np.float32(1e-8))
+
+
+def adam_step(theta, g, m, v, t, lr, b1=ADAM_B1, b2=ADAM_B2, eps=ADAM_EPS):
+    """Step t (t >= 1) of Adam (Kingma and Ba, ICLR 2015, Algorithm 1) in
+    float64: m <- b1 m + (1 - b1) g; v <- b2 v + (1 - b2) g^2;
+    m_hat = m / (1 - b1^t); v_hat = v / (1 - b2^t);
+    theta <- theta - lr m_hat / (sqrt(v_hat) + eps).  Returns (theta, m, v)."""
+    g = np.asarray(g, np.float64)
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    m_hat = m / (1.0 - b1 ** t)
+    v_hat = v / (1.0 - b2 ** t)
+    return np.asarray(theta, np.float64) - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
 def labels(nn, tour):
     """y[i][k] = 1 when (i, nn[i][k]) is an edge of the closed tour."""
     tour = np.asarray(tour)

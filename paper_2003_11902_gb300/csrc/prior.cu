@@ -532,6 +532,31 @@ mmas_status mmas_prior_get_params(mmas_prior *p, float *params)
     return MMAS_OK;
 }
 
+mmas_status mmas_prior_get_state(mmas_prior *p, float *m, float *v, float *grad, int32_t *step)
+{
+    if (!p) return pfail(nullptr, MMAS_EINVAL, "prior is NULL");
+    PCK(p, cudaDeviceSynchronize());
+    if (m) PCK(p, cudaMemcpy(m, p->adam_m, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (v) PCK(p, cudaMemcpy(v, p->adam_v, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (grad) PCK(p, cudaMemcpy(grad, p->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (step) *step = p->adam_t;
+    return MMAS_OK;
+}
+
+mmas_status mmas_prior_set_state(mmas_prior *p, const float *m, const float *v, int32_t step)
+{
+    if (!p || !m || !v) return pfail(p, MMAS_EINVAL, "prior, m and v must be non-NULL");
+    if (step < 0) return pfail(p, MMAS_EINVAL, "step must be >= 0");
+    for (int i = 0; i < NPARAM; ++i)
+        if (!(v[i] >= 0.0f) || !std::isfinite(v[i]) || !std::isfinite(m[i]))
+            return pfail(p, MMAS_EINVAL, "m must be finite and v finite and >= 0");
+    PCK(p, cudaDeviceSynchronize());
+    PCK(p, cudaMemcpy(p->adam_m, m, NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    PCK(p, cudaMemcpy(p->adam_v, v, NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    p->adam_t = step;
+    return MMAS_OK;
+}
+
 mmas_status mmas_prior_scores(mmas_prior *p, mmas_handle *h, float *scores)
 {
     if (!p || !scores) return pfail(p, MMAS_EINVAL, "prior and scores must be non-NULL");
@@ -609,7 +634,10 @@ mmas_status mmas_prior_train(mmas_prior *p, mmas_handle *h, const int32_t *tour,
             return st;
         // Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
         p->adam_t += 1;
-        const float c1 = 1.0f - powf(0.9f, (float)p->adam_t), c2 = 1.0f - powf(0.999f, (float)p->adam_t);
+        // bias corrections 1 - beta^t of the single-precision betas, in double
+        // (1 - beta2^t loses most of a float's digits to cancellation), rounded once
+        const float c1 = (float)(1.0 - pow((double)0.9f, (double)p->adam_t));
+        const float c2 = (float)(1.0 - pow((double)0.999f, (double)p->adam_t));
         k_adam<<<blocks_for(NPARAM), 256, 0, s>>>(p->params, p->grad, p->adam_m, p->adam_v, NPARAM, lr, 0.9f, 0.999f,
                                                   1e-8f, c1, c2);
         PCK(p, cudaGetLastError());

@@ -32,6 +32,7 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
            "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
            "mmas_prior_destroy", "mmas_prior_last_error", "mmas_prior_apply_weighted",
+           "mmas_prior_get_state", "mmas_prior_set_state",
            "mmas_batch_create", "mmas_batch_iterate", "mmas_batch_best_tour",
            "mmas_batch_best_lengths", "mmas_batch_get_tours", "mmas_batch_set_config",
            "mmas_batch_get_config", "mmas_batch_autotune", "mmas_batch_synchronize",
@@ -113,6 +114,8 @@ def load(path: str = LIB_PATH):
             "mmas_prior_create": (C.c_int, [P(f32), i32, P(H)]),
             "mmas_prior_set_params": (C.c_int, [H, P(f32)]),
             "mmas_prior_get_params": (C.c_int, [H, P(f32)]),
+            "mmas_prior_get_state": (C.c_int, [H, P(f32), P(f32), P(f32), P(i32)]),
+            "mmas_prior_set_state": (C.c_int, [H, P(f32), P(f32), i32]),
             "mmas_prior_scores": (C.c_int, [H, H, P(f32)]),
             "mmas_prior_train": (C.c_int, [H, H, P(i32), i32, f32, P(f32)]),
             "mmas_prior_grad": (C.c_int, [H, H, P(i32), P(f32), P(f32)]),
@@ -445,6 +448,20 @@ class Prior:
         out = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
         _pcheck(self._p, load().mmas_prior_get_params(self._p, _f32p(out)))
         return out
+
+    def state(self):
+        """(m, v, grad, step): Adam's moments, the last gradient and the step count."""
+        m = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
+        v = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
+        g = np.zeros(MMAS_PRIOR_PARAMS, np.float32)
+        t = C.c_int32()
+        _pcheck(self._p, load().mmas_prior_get_state(self._p, _f32p(m), _f32p(v), _f32p(g), C.byref(t)))
+        return m, v, g, t.value
+
+    def set_state(self, m, v, step: int):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        _pcheck(self._p, load().mmas_prior_set_state(self._p, _f32p(m), _f32p(v), int(step)))
 
     def scores(self, colony: "Colony"):
         out = np.zeros((colony.n, 16), np.float32)

@@ -354,6 +354,39 @@ def test_full_size_n1000_cl32_sampled_parity():
     g.close()
 
 
+def test_learned_prior_race_shape_n18500_cl16_sampled_parity():
+    """The largest race workload's colony shape (uniform n = 18,500, m = n,
+    cl = 16): the candidate table is staged only in part and the tabu lives in
+    shared memory.  Every tour is a permutation with an exact length; 25
+    sampled ants match the oracle pick for pick in iteration 0 and, after the
+    oracle applies the GPU's iteration best, in iteration 1; the pheromone
+    after that update agrees within 1e-5 relative."""
+    n = m = 18500
+    xy = I.uniform(n, 1018)
+    g = Colony(xy=xy, m=m, cl=16, rho=0.02, seed=1)
+    o = O.Colony(xy=xy, m=m, cl=16, rho=0.02, seed=1)
+    d = o.state()["d"]
+    kinds = []
+    for it in range(2):
+        g.iterate(1)
+        tours, lens = g.tours()
+        assert np.array_equal(np.sort(tours, axis=1), np.broadcast_to(np.arange(n, dtype=np.int32), (m, n)))
+        for k in range(0, m, 37):
+            assert lens[k] == O.tour_length(d, tours[k])
+        kinds += [check_ant(o, it, k, tours[k], lens[k]) for k in range(0, m, m // 25)][:25]
+        ib = int(np.argmin(lens))
+        o.update(tours[ib], int(lens[ib]))
+        del tours
+    st = g.stats()
+    assert st["construct_staged"] == 2 and st["iterations"] == 2
+    print(f"n=18500 sampled ants: {kinds.count('exact')} exact, {kinds.count('near_tie')} near-tie; "
+          f"fallbacks {st['fallback_steps']}, row scans {st['fallback_scans']}")
+    tau, tmin, tmax = g.pheromone()
+    assert (tmin, tmax) == o.limits()
+    np.testing.assert_allclose(tau, o.state()["tau"], rtol=1e-5, atol=0)
+    g.close()
+
+
 def test_full_size_n200_full_row_all_ants():
     n = m = 200
     xy = I.uniform(n, 1002)

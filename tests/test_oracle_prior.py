@@ -241,3 +241,50 @@ def test_whole_rounded_forward_stays_near_the_unrounded_one():
     sr, _ = P.forward(params, F, dn, nn, gpu_rounding=True)
     se, _ = P.forward(params, F, dn, nn, gpu_rounding=False)
     assert np.max(np.abs(sr - se)) < 1e-2 * (np.abs(se).max() + 1)
+
+
+# ---------------------------------------------------------------------------
+# Adam (Kingma and Ba, Algorithm 1)
+
+def test_adam_constant_gradient_closed_form():
+    # with m = v = 0 and a constant gradient g the bias corrections make
+    # m_hat = g and v_hat = g^2 at every step, so each step moves theta by
+    # lr g / (|g| + eps): t steps move it by t lr g / (|g| + eps)
+    g = np.array([3.0, -0.5, 1e-3, -2e-9, 0.0])
+    theta = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    m = np.zeros(5)
+    v = np.zeros(5)
+    lr = 0.01
+    th = theta.copy()
+    for t in range(1, 8):
+        th, m, v = P.adam_step(th, g, m, v, t, lr)
+    want = theta - 7 * lr * g / (np.abs(g) + P.ADAM_EPS)
+    np.testing.assert_allclose(th, want, rtol=0, atol=1e-12)
+
+
+def test_adam_moments_decay_after_one_gradient():
+    # one gradient g, then zeros: m_t = b1^(t-1) (1 - b1) g and
+    # v_t = b2^(t-1) (1 - b2) g^2
+    g = np.array([0.7, -1.3])
+    th, m, v = P.adam_step(np.zeros(2), g, np.zeros(2), np.zeros(2), 1, 0.1)
+    for t in range(2, 6):
+        th, m, v = P.adam_step(th, np.zeros(2), m, v, t, 0.1)
+    np.testing.assert_allclose(m, P.ADAM_B1 ** 4 * (1 - P.ADAM_B1) * g, rtol=1e-13)
+    np.testing.assert_allclose(v, P.ADAM_B2 ** 4 * (1 - P.ADAM_B2) * g * g, rtol=1e-13)
+
+
+def test_adam_matches_torch_optimizer():
+    # torch.optim.Adam implements the same algorithm; run both on the same
+    # gradient sequence in float64
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    theta0 = rng.standard_normal(50)
+    grads = rng.standard_normal((6, 50)) * rng.uniform(1e-4, 10, 50)
+    w = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([w], lr=0.05, betas=(P.ADAM_B1, P.ADAM_B2), eps=P.ADAM_EPS)
+    th, m, v = theta0.copy(), np.zeros(50), np.zeros(50)
+    for t, g in enumerate(grads, start=1):
+        w.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        th, m, v = P.adam_step(th, g, m, v, t, 0.05)
+    np.testing.assert_allclose(th, w.detach().numpy(), rtol=1e-12, atol=1e-14)
