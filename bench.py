@@ -13,9 +13,13 @@ beta = 2, p_best = 0.01 (synthetic coordinates, seed 1001).
   e2e          the same metric through the public C ABI with host buffers:
                mmas_create from host coordinates, then per step mmas_iterate
                and mmas_best_tour into host memory;
-  roofline     the construction kernel (the dominant one): algorithmic bytes
-               per launch / its mean CUDA-event duration, against the measured
-               HBM copy bandwidth;
+  roofline     the construction kernel (the dominant one): logical bytes per
+               launch (8 cl bytes a step: each candidate's 4-byte weight and
+               4-byte id) / its mean CUDA-event duration, against the measured
+               HBM copy bandwidth; roofline_l2 the same against the L2 read
+               bandwidth measured in the run, roofline_alu against the draw
+               rate (the bytes come from shared memory and L2, and the
+               step-to-step chain binds);
   cpu_baseline the CPU oracle (test infrastructure) on the host cores, a
                bounded sample of the same workload.
 
@@ -304,15 +308,50 @@ def _cfg(w):
 
 
 def algorithmic_construct_bytes(w):
-    """Bytes a construction launch must move: per step, cl candidate ids (2 B)
-    and reciprocal weights (4 B) -- or, without candidate lists, the n_unvisited
-    reciprocal weights (4 B each) -- plus the 4-byte tour entry per step."""
+    """Logical bytes a construction launch reads, counted as the method's unit
+    of work: per step, each of the cl candidates' weight (4 B) and id (4 B) --
+    8 cl bytes a step, 256 B at cl = 32 -- or, without candidate lists, the
+    weight (4 B) of each of the n - t unvisited nodes at step t."""
+    n, m, cl = w["n"], w["m"], w["cl"]
+    if cl > 0:
+        per_ant = (n - 1) * cl * 8
+    else:
+        per_ant = 4 * (n * (n - 1) // 2)
+    return m * per_ant
+
+
+def stored_construct_bytes(w):
+    """The same reads as this library stores them: 16-bit candidate ids (2 B)
+    and reciprocal weights (4 B) per candidate and step, plus the 4-byte tour
+    entry per step (whole rows: the unvisited weights and the tour entries)."""
     n, m, cl = w["n"], w["m"], w["cl"]
     if cl > 0:
         per_ant = (n - 1) * cl * 6 + 4 * n
     else:
         per_ant = 4 * (n * (n - 1) // 2) + 4 * n
     return m * per_ant
+
+
+def memory_rooflines(w, c_ms, dev, traffic=None):
+    """The construction kernel's logical bytes per second against the measured
+    HBM copy peak and against the L2 read bandwidth measured in this run
+    (mmas_probe_l2_bandwidth over a 32 MiB L2-resident buffer)."""
+    from paper_2003_11902_gb300 import mmas as _mm
+    peak, peak_kind = _peaks()
+    algo = algorithmic_construct_bytes(w)
+    achieved = algo / (c_ms * 1e-3) / 1e9
+    l2 = _mm.mmas_probe_l2_bandwidth(dev, 32 << 20)
+    hbm = {"kernel": "k_construct", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+           "algorithmic_bytes_per_launch": algo,
+           "bytes_per_step": algo / (w["m"] * (w["n"] - 1)),
+           "stored_bytes_per_launch": stored_construct_bytes(w),
+           "stored_frac": stored_construct_bytes(w) / (c_ms * 1e-3) / 1e9 / peak}
+    l2line = {"kernel": "k_construct", "bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s",
+              "frac": achieved / l2,
+              "peak_kind": "measured (mmas_probe_l2_bandwidth: 16-byte L2-only loads over a 32 MiB "
+                           "resident buffer, best of 10, same run)"}
+    return hbm, l2line
 
 
 # L* of a workload: the oracle's long-run best (tests/golden/make_lstar.py)
@@ -430,11 +469,8 @@ def run_ours(args, w):
         e2e_value = ws * w["m"] * args.steps / float(t.item())
 
     if rank == 0:
-        peak, peak_kind = _peaks()
         c_ms = statistics.mean(con)
-        algo = algorithmic_construct_bytes(w)
-        achieved = algo / (c_ms * 1e-3) / 1e9
-        traffic = _profiled_traffic(args.workload)
+        roof, roof_l2 = memory_rooflines(w, c_ms, dev, _profiled_traffic(args.workload))
         value = ws * w["m"] * args.steps / (total_ms * 1e-3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -447,10 +483,8 @@ def run_ours(args, w):
             "construct_ms": c_ms,
             "after_construct_ms": statistics.mean(t - c for t, c in zip(tot, con)),
             "construct_tours_per_s": w["m"] / (c_ms * 1e-3),
-            "roofline": {"kernel": "k_construct", "bound": "hbm", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": algo},
+            "roofline": roof,
+            "roofline_l2": roof_l2,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w["n"] / args.steps,
                     "d2h_bytes_per_step": 4 * w["n"] + 64},
             "gpu_launches": KERNELS_PER_ITERATION[w.get("ls", 0)] * args.steps,
@@ -879,10 +913,9 @@ def run_ours_prior(args, w):
     e2e_col.close()
     guided.close()
     prior.close()
-    peak, peak_kind = _peaks()
     c_ms = statistics.mean(con)
     wc = dict(w, n=w["n"], m=w["m"], cl=w["cl"])
-    algo = algorithmic_construct_bytes(wc)
+    roof, roof_l2 = memory_rooflines(wc, c_ms, 0)
     line = {
         "metric": METRIC, "value": w["m"] * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -896,9 +929,8 @@ def run_ours_prior(args, w):
                    "timing": "CUDA events in the iteration graph, launching stream"},
         "construct_ms": c_ms,
         "after_construct_ms": statistics.mean(t - c for t, c in zip(tot, con)),
-        "roofline": {"kernel": "k_construct", "bound": "hbm", "achieved": algo / (c_ms * 1e-3) / 1e9,
-                     "peak": peak, "unit": "GB/s", "frac": algo / (c_ms * 1e-3) / 1e9 / peak,
-                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": algo},
+        "roofline": roof,
+        "roofline_l2": roof_l2,
         "e2e": {"value": w["m"] * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 * w["n"] + 64,
                 "note": "create + apply the trained prior + per step iterate and read the best tour"},

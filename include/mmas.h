@@ -146,6 +146,8 @@ typedef struct {
     int32_t row_pitch;         /* elements per row of the n x n device matrices      */
     int64_t fallback_scans;    /* of the fallback steps, those that scanned the whole
                                   row (the rest were decided on the reach list)      */
+    int32_t construct_ants_per_warp; /* 1, or 2 when each half of a warp builds a tour
+                                  (candidate lists of at most 16, n > 4096, many ants) */
 } mmas_stats_t;
 
 /* Fill *p with the defaults listed at mmas_params (m = 0 means "m = n"). */
@@ -191,6 +193,39 @@ mmas_status mmas_construct(mmas_handle *h);
  * is not advanced.  Errors: EINVAL (not a permutation, len <= 0). */
 mmas_status mmas_update(mmas_handle *h, const int32_t *tour, int32_t len);
 
+/* ---- one colony sharded over ranks: the exchange on device buffers -------
+ *
+ * Ants are independent given the pheromone (Sec. 2.1), so rank r can build
+ * ants [ant_offset, ant_offset + m) of a colony of M ants (mmas_params.m = the
+ * rank's count, ant_offset its first global index; draws are keyed by the
+ * global index).  Alg. 1's iteration best over all ranks then takes, per
+ * iteration, after mmas_construct on every rank:
+ *   mmas_shard_best_key      -> all-reduce (MIN) of the 8-byte key,
+ *   mmas_shard_tour          -> all-reduce (SUM) of the n-int tour buffer,
+ *   mmas_update_device       (the same update on every replica),
+ * e.g. with NCCL on the colony's stream: 8 + 4n bytes per rank, no host copy.
+ * All three are enqueued on the colony's stream; pointers are DEVICE pointers
+ * on the colony's device.  Errors: EINVAL (NULL pointer), ECUDA. */
+
+/* *d_key (1 int64) = (L << 32) | (ant_offset + k) for the shortest tour k of
+ * the last construction (ties -> lower k): the all-reduced MIN of the ranks'
+ * keys is Alg. 1's iteration best over the whole colony. */
+mmas_status mmas_shard_best_key(mmas_handle *h, int64_t *d_key);
+
+/* d_tour (n int32) = the tour of global ant (*d_key & 0xFFFFFFFF) when this
+ * rank builds that ant, else n zeros: the element-wise SUM over the ranks is
+ * that tour on every rank. */
+mmas_status mmas_shard_tour(mmas_handle *h, const int64_t *d_key, int32_t *d_tour);
+
+/* mmas_update with a device-side tour d_tour (n int32) and length
+ * (*d_key >> 32): global best and limits, evaporation, deposit, choice_info;
+ * then the iteration index advances, as after a whole iteration, so that
+ * construct, exchange and update repeat with no host call in between.  The
+ * tour is checked on the device; if
+ * it is not a permutation of 0..n-1 (or the length is not positive) the update
+ * does nothing and the next synchronising call returns MMAS_ESTATE. */
+mmas_status mmas_update_device(mmas_handle *h, const int32_t *d_tour, const int64_t *d_key);
+
 /* Synchronise and copy the last constructed tours (m x n, row-major) and
  * their lengths (m).  Either pointer may be NULL. */
 mmas_status mmas_get_tours(mmas_handle *h, int32_t *tours, int32_t *lens);
@@ -215,6 +250,23 @@ mmas_status mmas_set_iteration(mmas_handle *h, int32_t it);
 
 /* Synchronise and fill *out. */
 mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out);
+
+/* Testing aid for the out-of-memory paths (not part of the method): arm a
+ * failure of the device allocation `after` allocations from now (0: the next
+ * one) made by mmas_create, mmas_batch_create, the learned prior's calls and
+ * the calls they make; that allocation fails as if the device were out of
+ * memory, the call returns MMAS_ENOMEM and frees what it had allocated, and
+ * the arming is spent.  after < 0 disarms.  Process-wide. */
+void mmas_debug_fail_allocation(int32_t after);
+
+/* Testing aid for the bounded device waits (not part of the method): with
+ * on != 0, every construction launch on `device` that stages its table in
+ * shared memory first waits for a flag that nothing sets, gives up after its
+ * 1 ms limit, lets its own bulk copies land (bounded, 2 s), records a timeout
+ * and leaves without building tours; the next synchronising call on the
+ * colony reports MMAS_ETIMEOUT and the colony's results are void.  on = 0
+ * restores normal waits.  Errors: EINVAL (bad device), ECUDA. */
+mmas_status mmas_debug_expire_stage_waits(int32_t device, int32_t on);
 
 /* Block until all work enqueued by the handle has finished; report device-side
  * errors (ETIMEOUT, ESTATE) raised since the last check. */
@@ -241,6 +293,16 @@ mmas_status mmas_phase_times(mmas_handle *h, float *construct_ms, float *rest_ms
  * per second to *draws_per_s.  Synchronous; allocates and frees a small device
  * buffer.  Errors: EINVAL (NULL output, ms <= 0), ECUDA. */
 mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s);
+
+/* Measurement aid (not part of the method): the L2 read bandwidth of device
+ * `device`, the ceiling for bytes that a kernel finds in L2 rather than in
+ * HBM.  A read-only kernel sweeps a `bytes`-byte buffer (small enough to stay
+ * resident in L2: 16-64 MiB on GB300) with 16-byte loads that bypass L1, many
+ * passes per launch at full occupancy; *gbs = the best of 10 launches in
+ * GB/s (10^9 bytes read per second).  Synchronous; allocates and frees the
+ * buffer.  Errors: EINVAL (NULL gbs, bytes outside [1 MiB, 1 GiB]), ENOMEM,
+ * ECUDA. */
+mmas_status mmas_probe_l2_bandwidth(int32_t device, int64_t bytes, double *gbs);
 
 /* ---- learned edge prior: tensor-core GEMM ---------------------------------
  *

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SO = os.path.join(HERE, "libmmas.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["setup.cu", "construct.cu", "pheromone.cu", "twoopt.cu", "runtime.cu", "batch.cu", "measure.cu", "gemm.cu", "prior.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "construct.cu", "pheromone.cu", "twoopt.cu", "runtime.cu", "batch.cu", "measure.cu", "gemm.cu", "prior.cu", "noalloc.cu", "shard.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("internal.cuh", "twoopt.cuh", "distance.cuh", "handle.cuh")] + [os.path.join(INCLUDE, "mmas.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]

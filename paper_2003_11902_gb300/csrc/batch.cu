@@ -211,7 +211,7 @@ mmas_status build_chunks(mmas_batch *b, int w)
     if ((int)ch.size() > b->chunk_cap) {
         if (b->d_chunks) cudaFree(b->d_chunks);
         b->d_chunks = nullptr;
-        BCK(b, cudaMalloc(&b->d_chunks, ch.size() * sizeof(BatchChunk)));
+        BCK(b, device_malloc(&b->d_chunks, ch.size() * sizeof(BatchChunk)));
         b->chunk_cap = (int)ch.size();
     }
     BCK(b, cudaMemcpyAsync(b->d_chunks, ch.data(), ch.size() * sizeof(BatchChunk),
@@ -338,7 +338,7 @@ mmas_status create_batch(mmas_batch *b, const mmas_instance *insts, int count, c
     b->alpha1 = p.alpha == 1.0f;
     auto upload = [&](auto **dst, const auto &v) -> mmas_status {
         const size_t bytes = v.size() * sizeof(v[0]);
-        BCK(b, cudaMalloc(reinterpret_cast<void **>(dst), bytes));
+        BCK(b, device_malloc(reinterpret_cast<void **>(dst), bytes));
         BCK(b, cudaMemcpyAsync(*dst, v.data(), bytes, cudaMemcpyHostToDevice, b->stream));
         return MMAS_OK;
     };
@@ -351,9 +351,9 @@ mmas_status create_batch(mmas_batch *b, const mmas_instance *insts, int count, c
     if ((st = upload(&b->d_row_colony, row_colony)) != MMAS_OK) return st;
     if ((st = upload(&b->d_row_base, row_base)) != MMAS_OK) return st;
     if ((st = upload(&b->d_scs, scs)) != MMAS_OK) return st;
-    BCK(b, cudaMalloc(&b->d_counter, sizeof(unsigned)));
-    BCK(b, cudaMalloc(&b->d_best, (size_t)B * sizeof(int32_t)));
-    BCK(b, cudaMalloc(&b->d_gather, 2 * sizeof(unsigned long long)));
+    BCK(b, device_malloc(&b->d_counter, sizeof(unsigned)));
+    BCK(b, device_malloc(&b->d_best, (size_t)B * sizeof(int32_t)));
+    BCK(b, device_malloc(&b->d_gather, 2 * sizeof(unsigned long long)));
     BCK(b, cudaMallocHost(&b->h_best, (size_t)B * sizeof(int32_t)));
     BCK(b, cudaMallocHost(&b->h_gather, 2 * sizeof(unsigned long long)));
     BCK(b, cudaStreamSynchronize(b->stream));

@@ -29,6 +29,13 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr unsigned long long STAGE_LIMIT_NS = 2000000000ull;  // 2 s
+constexpr unsigned long long EXPIRE_LIMIT_NS = 1000000ull;    // 1 ms
+
+// Testing aid (mmas_debug_expire_stage_waits): when set, every staging first
+// waits for g_never_set, which nothing writes, until its 1 ms limit runs out,
+// and then takes the timeout path.
+__device__ uint32_t g_expire_stage_waits;
+__device__ uint32_t g_never_set;
 constexpr uint32_t BULK_CHUNK = 32768u;
 
 enum { CAND = 0, ROW = 1 };
@@ -550,6 +557,225 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two ants per warp: candidate lists of at most 16 entries with the tabu in
+// shared memory.  Lanes 0-15 build one ant's tour and lanes 16-31 another's in
+// the same instructions: lane l scores slot l & 15 of its ant's list and each
+// half reduces its keys under its own mask.  Draws, picks, fallbacks and tours
+// are exactly those of one ant per warp (the same counters, the same ties).
+// ---------------------------------------------------------------------------
+
+// Score slot `slot` of row cur for the enabled half; the half's largest key in
+// mx (0: no unvisited candidate) and its node (ties -> lower id).
+template <bool PART>
+__device__ __forceinline__ uint32_t pair_pick(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                              const uint32_t *tw, int cur, int slot, unsigned hmask,
+                                              bool en, float lg, uint32_t &mx)
+{
+    const bool act = en && slot < a.cl;
+    uint32_t v;
+    float wi;
+    cand_load<PART>(a, cc, cw, cur, act ? cur * a.cl + slot : 0, v, wi);
+    const uint32_t word = tw[v >> 5];
+    const bool ok = act && !((word >> (v & 31)) & 1u);
+    const uint32_t k = ok ? neg_key(__fmul_rn(lg, wi)) : 0u;
+    mx = __reduce_max_sync(hmask, k);
+    return __reduce_min_sync(hmask, k == mx ? v : 0xFFFFFFFFu);
+}
+
+// Per-lane view of the two ants of a warp.
+struct PairCtx {
+    int lane, half, slot;  // slot = lane & 15
+    unsigned hmask;        // this half's lanes
+    uint32_t *tbase;       // the warp's tabus: half h at tbase + h nw
+    uint32_t *tw;          // this half's tabu
+    int nw;
+    int ant;               // this half's ant (global index, keys the draws)
+    bool wr;               // this half's ant is real (writes its tour and counts)
+};
+
+// The greedy / sampled fallback of half h's ant, run by the whole warp; every
+// lane returns the node, and the half's lanes count it.
+__device__ __forceinline__ int pair_fallback(const ConstructArgs &a, const PairCtx &c, int h, int cur, int t,
+                                             uint32_t it, unsigned long long &fbn)
+{
+    const int hc = __shfl_sync(FULL, cur, 16 * h);
+    const int hant = __shfl_sync(FULL, c.ant, 16 * h);
+    Tabu<0> tb;
+    tb.w = c.tbase + (size_t)h * c.nw;
+    tb.nw = c.nw;
+    const int r = cand_fallback<0>(a.wmat + (size_t)hc * a.ld, a.n, tb, c.lane, a.fallback, (uint32_t)t,
+                                   (uint32_t)hant, it, a.key0, a.key1, &a.sc->err, hc,
+                                   a.xlw + (size_t)hc * a.xe, a.xlb + hc,
+                                   a.xxw + (size_t)hc * REACH_EXTRA, a.xxn + hc, a.xe);
+    unsigned long long dummy = 0;
+    const int node = count_fallback(r, c.half == h ? fbn : dummy);
+    return node;
+}
+
+// Half h takes node `node` as its step-t entry: mark, window slot, cur.
+__device__ __forceinline__ void pair_take(const PairCtx &c, int h, int node, int t, int &cur, int &twin)
+{
+    if (c.half == h) {
+        if (c.slot == 0) c.tw[node >> 5] |= 1u << (node & 31);
+        twin = (c.slot == (t & 15)) ? node : twin;
+        cur = node;
+    }
+    __syncwarp();
+}
+
+// Step t for half h alone (the other half idles), with its fallback.
+template <bool PART>
+__device__ __forceinline__ void pair_step_half(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                               const PairCtx &c, int h, int t, float lg, uint32_t it,
+                                               int &cur, int &twin, unsigned long long &fbn)
+{
+    uint32_t mx;
+    const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, c.half == h, lg, mx);
+    const uint32_t hmx = __shfl_sync(FULL, mx, 16 * h);
+    const int node = hmx != 0u ? (int)__shfl_sync(FULL, nxt, 16 * h) : pair_fallback(a, c, h, cur, t, it, fbn);
+    pair_take(c, h, node, t, cur, twin);
+}
+
+// Step t for both halves one after the other where a fallback is needed.
+template <bool PART>
+__device__ __forceinline__ void pair_step_both(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                               const PairCtx &c, int t, float lg, uint32_t it, int &cur,
+                                               int &twin, unsigned long long &fbn)
+{
+    uint32_t mx;
+    const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, true, lg, mx);
+    const unsigned frozen = __ballot_sync(FULL, mx == 0u);
+    if (c.slot == 0 && mx != 0u) c.tw[nxt >> 5] |= 1u << (nxt & 31);
+    twin = (mx != 0u && c.slot == (t & 15)) ? (int)nxt : twin;
+    cur = mx != 0u ? (int)nxt : cur;
+    __syncwarp();
+    for (int h = 0; h < 2; ++h)
+        if ((frozen >> (16 * h)) & 0xFFFFu) pair_take(c, h, pair_fallback(a, c, h, cur, t, it, fbn), t, cur, twin);
+}
+
+// Store half-window w (steps 16w .. t_end) of this lane's ant: slot s holds
+// entry 16w + s.
+__device__ __forceinline__ void pair_store(const PairCtx &c, int32_t *trow, int w, int t_end, int twin)
+{
+    if (c.wr && c.slot <= t_end - 16 * w) trow[16 * w + c.slot] = twin;
+}
+
+// The generator call of group g + 1 spread over the four steps of group g.
+__device__ __forceinline__ void pair_gen(const ConstructArgs &a, uint4 &nx, float (&nl)[4], int j)
+{
+    if (j == 0) philox_rounds_rk<0, 4>(nx, a.rk0, a.rk1);
+    if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
+    if (j == 2) {
+        philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
+        nl[0] = log2f(unit_open(nx.x));
+        nl[1] = log2f(unit_open(nx.y));
+    }
+    if (j == 3) {
+        nl[2] = log2f(unit_open(nx.z));
+        nl[3] = log2f(unit_open(nx.w));
+    }
+}
+
+// Group g (steps 4g .. 4g+3) with checks: steps t = 0 and t >= n are skipped
+// and windows stored as they complete (first and last groups).
+template <bool PART>
+__device__ __forceinline__ void pair_group_checked(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                                   const PairCtx &c, int32_t *trow, uint32_t it, int g,
+                                                   float (&lg)[4], int &cur, int &twin,
+                                                   unsigned long long &fbn)
+{
+    uint4 nx = make_uint4((uint32_t)c.slot, (uint32_t)(g + 1), (uint32_t)c.ant, it);
+    float nl[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pair_gen(a, nx, nl, j);
+        const int t = 4 * g + j;
+        if (t == 0 || t >= a.n) continue;
+        pair_step_both<PART>(a, cc, cw, c, t, lg[j], it, cur, twin, fbn);
+        if ((t & 15) == 15 || t == a.n - 1) pair_store(c, trow, t >> 4, t, twin);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
+}
+
+// A full group inside the tour: a half whose candidates are all visited
+// freezes for the rest of the group; afterwards each frozen half takes its
+// fallback and its remaining steps alone.  Equal to four checked steps.
+template <bool PART>
+__device__ __forceinline__ void pair_group(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                           const PairCtx &c, uint32_t it, int g, float (&lg)[4], int &cur,
+                                           int &twin, unsigned long long &fbn)
+{
+    uint4 nx = make_uint4((uint32_t)c.slot, (uint32_t)(g + 1), (uint32_t)c.ant, it);
+    float nl[4];
+    const int tb16 = (4 * g) & 15;
+    bool live = true;  // uniform within the half
+    int jfail = 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pair_gen(a, nx, nl, j);
+        uint32_t mx;
+        const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, true, lg[j], mx);
+        jfail = (live && mx == 0u) ? j : jfail;
+        live = live && mx != 0u;
+        if (c.slot == 0 && live) c.tw[nxt >> 5] |= 1u << (nxt & 31);
+        twin = (live && c.slot == tb16 + j) ? (int)nxt : twin;
+        cur = live ? (int)nxt : cur;
+        __syncwarp();
+    }
+    const unsigned frozen = __ballot_sync(FULL, jfail < 4);
+    if (__builtin_expect(frozen != 0u, 0)) {
+        for (int h = 0; h < 2; ++h) {
+            if (!((frozen >> (16 * h)) & 0xFFFFu)) continue;
+            const int hj = __shfl_sync(FULL, jfail, 16 * h);
+            pair_take(c, h, pair_fallback(a, c, h, cur, 4 * g + hj, it, fbn), 4 * g + hj, cur, twin);
+            for (int j = hj + 1; j < 4; ++j) pair_step_half<PART>(a, cc, cw, c, h, 4 * g + j, lg[j], it, cur, twin, fbn);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
+}
+
+// The tours of a pair of ants (this lane's half builds c.ant's).
+template <bool PART>
+__device__ __forceinline__ void build_tour_pair(const ConstructArgs &a, const uint16_t *cc, const float *cw,
+                                                PairCtx &c, uint32_t it, int32_t *trow)
+{
+    uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)c.ant, it);
+    philox_rounds<0, 10>(s4, a.key0, a.key1);
+    const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
+    for (int q = c.slot; q < c.nw; q += 16) c.tw[q] = 0u;
+    __syncwarp();
+    if (c.slot == 0) c.tw[start >> 5] |= 1u << (start & 31);
+    __syncwarp();
+    int cur = start, twin = start;
+    unsigned long long fbn = 0;
+    float lg[4];
+    {
+        uint4 r = make_uint4((uint32_t)c.slot, 0u, (uint32_t)c.ant, it);
+        philox_rounds<0, 10>(r, a.key0, a.key1);
+        lg[0] = 0.0f;  // step 0 is the start node
+        lg[1] = log2f(unit_open(r.y));
+        lg[2] = log2f(unit_open(r.z));
+        lg[3] = log2f(unit_open(r.w));
+    }
+    pair_group_checked<PART>(a, cc, cw, c, trow, it, 0, lg, cur, twin, fbn);
+    int g = 1;
+    for (; 4 * g + 3 <= a.n - 1; ++g) {
+        pair_group<PART>(a, cc, cw, c, it, g, lg, cur, twin, fbn);
+        if ((g & 3) == 3) pair_store(c, trow, g >> 2, 4 * g + 3, twin);
+    }
+    if (4 * g <= a.n - 1)
+        pair_group_checked<PART>(a, cc, cw, c, trow, it, g, lg, cur, twin, fbn);
+    else if (g > 1 && ((g - 1) & 3) != 3)
+        pair_store(c, trow, (g - 1) >> 2, a.n - 1, twin);  // the last full group ended it
+    if (c.wr && c.slot == 0 && fbn) {
+        atomicAdd(&a.sc->fallback_steps, fbn & 0xFFFFFFFFull);
+        if (fbn >> 32) atomicAdd(&a.sc->fallback_scans, fbn >> 32);
+    }
+}
+
 // Stage `bytes_w` bytes of weights and `bytes_c` of ids into shared memory
 // with the bulk-copy engine (thread 0 issues, every thread waits on the
 // mbarrier, bounded).  Returns false on a timeout, after which the CTA must
@@ -569,6 +795,14 @@ __device__ __forceinline__ bool stage_table(unsigned char *s_w, const void *src_
         const unsigned char *sc = static_cast<const unsigned char *>(src_c);
         for (uint32_t o = 0; o < bytes_c; o += BULK_CHUNK)
             bulk_copy_g2s(s_c + o, sc + o, min(BULK_CHUNK, bytes_c - o), bar);
+    }
+    if (*reinterpret_cast<volatile uint32_t *>(&g_expire_stage_waits)) {
+        const unsigned long long t0 = global_ns();
+        while (!*reinterpret_cast<volatile uint32_t *>(&g_never_set) && global_ns() - t0 < EXPIRE_LIMIT_NS) {
+        }
+        if (threadIdx.x == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
+        mbar_wait_bounded(bar, parity, STAGE_LIMIT_NS);  // the copies land before the CTA leaves
+        return false;
     }
     if (!mbar_wait_bounded(bar, parity, STAGE_LIMIT_NS)) {
         if (threadIdx.x == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
@@ -619,6 +853,52 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
     int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
     for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride)
         build_tour<MODE, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
+}
+
+// Two ants per warp (candidate lists of at most 16, tabu in shared memory).
+// STAGED as for k_construct.  Warp w of the grid builds ants 2w and 2w + 1 of
+// each round; with an odd count the second half of the last warp repeats the
+// first half's ant without writing it.
+template <int STAGED>
+__global__ void __launch_bounds__(384, 1) k_construct_pair(const ConstructArgs a, int cons_warps)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t it = (uint32_t)a.iter[0];
+    const float *cw = a.cwinv;
+    const uint16_t *cc = a.cand16;
+    size_t off = 0;
+    if constexpr (STAGED != 0) {
+        unsigned char *s_w = smem;
+        off = a.stage_w_bytes;
+        unsigned char *s_c = smem + off;
+        off += a.stage_c_bytes;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
+        off += 16;
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (!stage_table(s_w, cw, a.stage_w_bytes, s_c, a.cand16, a.stage_c_bytes, bar, 0, &a.sc->err))
+            return;
+        cw = reinterpret_cast<const float *>(s_w);
+        cc = reinterpret_cast<const uint16_t *>(s_c);
+    }
+    PairCtx c;
+    c.lane = lane;
+    c.half = lane >> 4;
+    c.slot = lane & 15;
+    c.hmask = c.half ? 0xFFFF0000u : 0x0000FFFFu;
+    c.nw = (a.n + 31) >> 5;
+    c.tbase = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * 2 * c.nw;
+    c.tw = c.tbase + (size_t)c.half * c.nw;
+    const int stride = 2 * gridDim.x * cons_warps;
+    const int ant_end = a.ant_offset + a.m;
+    int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
+    for (int a0 = a.ant_offset + 2 * (blockIdx.x * cons_warps + warp); a0 < ant_end; a0 += stride) {
+        const int mine = a0 + c.half;
+        c.wr = mine < ant_end;
+        c.ant = c.wr ? mine : a0;
+        build_tour_pair<STAGED == 2>(a, cc, cw, c, it, tours_g + (size_t)c.ant * a.ld);
+    }
 }
 
 // Batched construction: one persistent launch builds every ant of
@@ -1006,6 +1286,11 @@ KernelFn pick_kernel(int mode, int staged, int tw)
     return mode == CAND ? cand[staged][ti] : rowk[staged ? 1 : 0][ti];
 }
 
+KernelFn pick_kernel_pair(int staged)
+{
+    return staged == 1 ? k_construct_pair<1> : (staged == 2 ? k_construct_pair<2> : k_construct_pair<0>);
+}
+
 // whole-row variants: (sel, ct) != (0, 0); TW 1 (n <= 1024) or 0 for the bitmask
 KernelFn pick_kernel_var(int sel, int ct, int staged, int tw)
 {
@@ -1019,6 +1304,12 @@ KernelFn pick_kernel_var(int sel, int ct, int staged, int tw)
 
 }  // namespace
 
+cudaError_t set_stage_wait_expiry(bool on)
+{
+    const uint32_t v = on ? 1u : 0u;
+    return cudaMemcpyToSymbol(g_expire_stage_waits, &v, sizeof(v));
+}
+
 cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
                            ConstructPlan *plan)
 {
@@ -1026,15 +1317,19 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const bool var = row && (a.sel != 0 || a.ct != 0);
     const int nw = (a.n + 31) / 32;
     plan->tw = var ? (a.n <= 1024 ? 1 : 0) : tabu_words(a.n);
+    // two ants per warp: short candidate lists (half a warp scores one list),
+    // shared-memory tabus, and more ants than one-ant warps could carry
+    plan->pair = !row && a.cl <= 16 && plan->tw == 0 && a.m > 12 * num_sms;
+    const int per_ants = plan->pair ? 2 : 1;  // ants a warp builds at once
     // per-warp shared memory besides the table: the compact list, or the tabu
-    // bitmask when it does not live in registers
+    // bitmasks when they do not live in registers
     const size_t per_warp = (var && a.ct) ? (((size_t)a.n * 2 + 15) & ~size_t(15))
-                                          : (plan->tw ? 0 : (size_t)nw * sizeof(uint32_t));
+                                          : (plan->tw ? 0 : (size_t)per_ants * nw * sizeof(uint32_t));
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
     // staged: one CTA per SM (the table fills its shared memory) carrying
     // ceil(m / #SMs) ants, at most 12 warps; warps loop over further ants
-    int w = (a.m + num_sms - 1) / num_sms;
+    int w = (a.m + per_ants * num_sms - 1) / (per_ants * num_sms);
     w = w < 1 ? 1 : (w > 12 ? 12 : w);
     const size_t masks = (size_t)w * per_warp;
     const size_t need = table + 16 + masks;
@@ -1043,11 +1338,12 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const size_t avail = smem_optin > 16 + masks ? smem_optin - 16 - masks : 0;
     const int part_rows = row ? 0 : (int)(avail / ((size_t)a.cl * 6)) & ~7;
     plan->stage_rows = a.n;
+    const int wave = per_ants * w;  // ants a CTA builds at once
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
         plan->cons_warps = w;
         plan->gen_warps = 0;
-        const int g = (a.m + w - 1) / w;
+        const int g = (a.m + wave - 1) / wave;
         plan->grid = g < num_sms ? g : num_sms;
         plan->smem = need;
     } else if (!var && part_rows >= 64 && part_rows < a.n) {
@@ -1055,18 +1351,19 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->stage_rows = part_rows;
         plan->cons_warps = w;
         plan->gen_warps = 0;
-        const int g = (a.m + w - 1) / w;
+        const int g = (a.m + wave - 1) / wave;
         plan->grid = g < num_sms ? g : num_sms;
         plan->smem = (size_t)part_rows * a.cl * 6 + 16 + masks;
     } else {
         plan->staged = 0;
         plan->cons_warps = 4;
         plan->gen_warps = 0;
-        plan->grid = (a.m + 3) / 4;
+        plan->grid = (a.m + 4 * per_ants - 1) / (4 * per_ants);
         plan->smem = (size_t)4 * per_warp;
     }
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan->staged, plan->tw)
-                     : pick_kernel(row ? ROW : CAND, plan->staged, plan->tw);
+                     : (plan->pair ? pick_kernel_pair(plan->staged)
+                                   : pick_kernel(row ? ROW : CAND, plan->staged, plan->tw));
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
 }
@@ -1107,7 +1404,8 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
     }
     const bool var = a.cl == 0 && (a.sel != 0 || a.ct != 0);
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan.staged, plan.tw)
-                     : pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw);
+                     : (plan.pair ? pick_kernel_pair(plan.staged)
+                                  : pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw));
     k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();
 }

@@ -28,6 +28,7 @@ struct mmas_handle {
     mmas::Scalars *sc = nullptr;
     int *maxd = nullptr;
     int32_t *ext_tour = nullptr, *ext_len = nullptr;
+    uint32_t *ext_bad = nullptr;     // set when a device-side tour was refused (skip that update)
     int32_t *nnd = nullptr;
     int32_t xe = 0;                  // reach-list length of the greedy fallback (0: none)
     int32_t *xl32 = nullptr;         // [n][xe]

@@ -17,6 +17,7 @@ enum : uint32_t {
     ERR_STAGE_TIMEOUT = 1u,   // a shared-memory staging wait gave up
     ERR_NO_UNVISITED = 2u,    // a selection found no unvisited node (inconsistent tabu)
     ERR_LS_CAP = 4u,          // a local search exceeded its move cap and stopped
+    ERR_BAD_TOUR = 8u,        // a device-side tour handed to the update was not a permutation
 };
 
 // Device-resident scalars of one colony.  Kernels read and write them, so a
@@ -233,6 +234,7 @@ struct ConstructPlan {
     int staged;     // 0: no staging; 1: the whole table in shared memory; 2: its first stage_rows rows
     int stage_rows;
     int tw;         // tabu words per lane in registers (1, 2, 4; n <= 1024 tw), 0: shared memory
+    int pair;       // 1: two ants per warp (half a warp each; cl <= 16, tw = 0)
     int cons_warps; // warps building tours (one ant each) per CTA
     int gen_warps;  // reserved (0)
     int grid;
@@ -248,6 +250,7 @@ struct BestArgs {
     int32_t *gb_tour;      // [n]
     int2 *nbr;             // [n]: successor and predecessor in the deposited tour
     Scalars *sc;
+    const uint32_t *skip;  // nullptr, or a device flag: when set the step does nothing
 };
 
 struct ScoreArgs {
@@ -280,10 +283,20 @@ struct UpdateArgs {
     int32_t *xhot;        // [n] nodes above tau_min outside the list at the last pass
     float *xlb;           // [n] max choice_info over the other nodes j != i with eta^beta_ij at
                           // most that of the last listed node
+    const uint32_t *skip; // nullptr, or a device flag: when set the pass does nothing
 };
 
 // Message returned by mmas_last_error(NULL) on the calling thread.
 void set_thread_error(const std::string &msg);
+
+// Every device allocation of a colony, a batch or a learned prior: cudaMalloc,
+// or cudaErrorMemoryAllocation when mmas_debug_fail_allocation armed a failure.
+cudaError_t device_malloc(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t device_malloc(T **p, size_t bytes)
+{
+    return device_malloc(reinterpret_cast<void **>(p), bytes);
+}
 
 // ---------------------------------------------------------------------------
 // Host launchers (return the launch's cudaError_t)
@@ -300,6 +313,9 @@ cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tou
 cudaError_t launch_init_colony(int32_t n, int32_t ld, double rho, double p_root, float *tau,
                                Scalars *sc, cudaStream_t s);
 
+// Testing aid: make every staging wait of the construction kernels on the
+// current device run out (ERR_STAGE_TIMEOUT) or behave normally again.
+cudaError_t set_stage_wait_expiry(bool on);
 cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_optin,
                            ConstructPlan *plan);
 cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, cudaStream_t s);

@@ -1,5 +1,6 @@
-// Measurement aid: the arithmetic ceiling of one selection (mmas_probe_draw_rate,
-// include/mmas.h).
+// Measurement aids: the arithmetic ceiling of one selection
+// (mmas_probe_draw_rate) and the L2 read bandwidth (mmas_probe_l2_bandwidth),
+// both declared in include/mmas.h.
 //
 // A candidate-list step costs, per candidate slot, one Philox4x32-10 output
 // word (a call yields four), the (0,1) uniform, an accurate log2, the key
@@ -34,10 +35,81 @@ __global__ void __launch_bounds__(256) k_draw_probe(ConstructArgs a, int iters, 
     out[g] = best;
 }
 
+// Read-only sweep of a buffer that stays resident in L2: every thread loads
+// 16-byte words with a grid stride, `passes` times, through L2 only
+// (ld.global.cg skips L1), and folds them into one word so no load is dead.
+__global__ void __launch_bounds__(256) k_l2_probe(const uint4 *__restrict__ buf, size_t words, int passes,
+                                                  uint32_t *out)
+{
+    const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (int p = 0; p < passes; ++p) {
+#pragma unroll 4
+        for (size_t i = g; i < words; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    out[g] = acc;
+}
+
 }  // namespace
 }  // namespace mmas
 
 using namespace mmas;
+
+extern "C" mmas_status mmas_probe_l2_bandwidth(int32_t device, int64_t bytes, double *gbs)
+{
+    if (!gbs || bytes < (1 << 20) || bytes > (int64_t)1 << 30) {
+        set_thread_error("mmas_probe_l2_bandwidth: gbs must be non-NULL and 1 MiB <= bytes <= 1 GiB");
+        return MMAS_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, device);
+    uint4 *buf = nullptr;
+    uint32_t *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 0.0;
+    const size_t words = (size_t)bytes / sizeof(uint4);
+    if (e == cudaSuccess) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_probe, 256, 0);
+        const int grid = prop.multiProcessorCount * (per_sm > 0 ? per_sm : 1);
+        if (e == cudaSuccess) e = cudaMalloc(&buf, words * sizeof(uint4));
+        if (e == cudaSuccess) e = cudaMemset(buf, 0x5A, words * sizeof(uint4));
+        if (e == cudaSuccess) e = cudaMalloc(&out, (size_t)grid * 256 * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        // about 1 ms a launch at tens of TB/s
+        const int passes = (int)std::max<int64_t>(1, ((int64_t)32 << 30) / bytes);
+        if (e == cudaSuccess) k_l2_probe<<<grid, 256>>>(buf, words, 1, out);  // bring it into L2
+        for (int r = 0; e == cudaSuccess && r < 10; ++r) {
+            cudaEventRecord(e0);
+            k_l2_probe<<<grid, 256>>>(buf, words, passes, out);
+            cudaEventRecord(e1);
+            e = cudaEventSynchronize(e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e == cudaSuccess && t > 0.0f)
+                best = std::max(best, (double)words * sizeof(uint4) * passes / (t * 1e-3) / 1e9);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (buf) cudaFree(buf);
+    if (out) cudaFree(out);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("mmas_probe_l2_bandwidth: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? MMAS_ENOMEM : MMAS_ECUDA;
+    }
+    *gbs = best;
+    return MMAS_OK;
+}
 
 extern "C" mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s)
 {

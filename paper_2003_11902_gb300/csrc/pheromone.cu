@@ -93,7 +93,11 @@ __device__ void select_best(const BestArgs &a)
     }
 }
 
-__global__ void __launch_bounds__(1024) k_best(const BestArgs a) { select_best(a); }
+__global__ void __launch_bounds__(1024) k_best(const BestArgs a)
+{
+    if (a.skip && *a.skip) return;
+    select_best(a);
+}
 
 // Length of one tour, summed by the whole CTA (the result is valid in thread
 // 0).  Each thread takes four consecutive edges per round (an int4 of the tour
@@ -318,6 +322,7 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
 template <bool FULLROW, bool ALPHA1>
 __global__ void __launch_bounds__(256, 4) k_update_cta(const UpdateArgs a)
 {
+    if (a.skip && *a.skip) return;
     const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
     for (int i = blockIdx.x; i < a.n; i += gridDim.x) update_row_cta<FULLROW, ALPHA1, true>(a, i, tmin, tmax, delta);
 }
@@ -438,6 +443,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
 template <bool FULLROW, bool ALPHA1>
 __global__ void __launch_bounds__(256, 4) k_update(const UpdateArgs a)
 {
+    if (a.skip && *a.skip) return;
     const float tmin = a.sc->tmin, tmax = a.sc->tmax, delta = a.sc->delta;
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);

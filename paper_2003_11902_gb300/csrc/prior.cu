@@ -366,31 +366,31 @@ mmas_status ensure(mmas_prior *p, int n)
     if (n <= p->cap) return MMAS_OK;
     free_work(p);
     const size_t N = (size_t)n;
-    PCK(p, cudaMalloc(&p->ext, 8 * sizeof(int)));
-    PCK(p, cudaMalloc(&p->F, N * FIN * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->FT, N * FIN * sizeof(bf16)));
+    PCK(p, device_malloc(&p->ext, 8 * sizeof(int)));
+    PCK(p, device_malloc(&p->F, N * FIN * sizeof(bf16)));
+    PCK(p, device_malloc(&p->FT, N * FIN * sizeof(bf16)));
     for (int l = 0; l < 4; ++l) {
-        PCK(p, cudaMalloc(&p->hb[l], N * H * sizeof(bf16)));
-        PCK(p, cudaMalloc(&p->h[l], N * H * sizeof(float)));
-        PCK(p, cudaMalloc(&p->z[l], N * 2 * H * sizeof(bf16)));
+        PCK(p, device_malloc(&p->hb[l], N * H * sizeof(bf16)));
+        PCK(p, device_malloc(&p->h[l], N * H * sizeof(float)));
+        PCK(p, device_malloc(&p->z[l], N * 2 * H * sizeof(bf16)));
     }
-    PCK(p, cudaMalloc(&p->zT, N * 2 * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->dab, N * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->daT, N * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->hbT, N * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->dqb, N * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->dqT, N * H * sizeof(bf16)));
-    PCK(p, cudaMalloc(&p->dn, N * KN * sizeof(float)));
-    PCK(p, cudaMalloc(&p->q, N * H * sizeof(float)));
-    PCK(p, cudaMalloc(&p->s, N * KN * sizeof(float)));
-    PCK(p, cudaMalloc(&p->y, N * KN * sizeof(float)));
-    PCK(p, cudaMalloc(&p->dh, N * H * sizeof(float)));
-    PCK(p, cudaMalloc(&p->dhp, N * H * sizeof(float)));
-    PCK(p, cudaMalloc(&p->dz, N * 2 * H * sizeof(float)));
-    PCK(p, cudaMalloc(&p->dq, N * H * sizeof(float)));
-    PCK(p, cudaMalloc(&p->nn, N * KN * sizeof(int32_t)));
-    PCK(p, cudaMalloc(&p->tour, N * sizeof(int32_t)));
-    PCK(p, cudaMalloc(&p->sp, N * sizeof(int2)));
+    PCK(p, device_malloc(&p->zT, N * 2 * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->dab, N * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->daT, N * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->hbT, N * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->dqb, N * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->dqT, N * H * sizeof(bf16)));
+    PCK(p, device_malloc(&p->dn, N * KN * sizeof(float)));
+    PCK(p, device_malloc(&p->q, N * H * sizeof(float)));
+    PCK(p, device_malloc(&p->s, N * KN * sizeof(float)));
+    PCK(p, device_malloc(&p->y, N * KN * sizeof(float)));
+    PCK(p, device_malloc(&p->dh, N * H * sizeof(float)));
+    PCK(p, device_malloc(&p->dhp, N * H * sizeof(float)));
+    PCK(p, device_malloc(&p->dz, N * 2 * H * sizeof(float)));
+    PCK(p, device_malloc(&p->dq, N * H * sizeof(float)));
+    PCK(p, device_malloc(&p->nn, N * KN * sizeof(int32_t)));
+    PCK(p, device_malloc(&p->tour, N * sizeof(int32_t)));
+    PCK(p, device_malloc(&p->sp, N * sizeof(int2)));
     p->cap = n;
     return MMAS_OK;
 }
@@ -486,7 +486,7 @@ mmas_status mmas_prior_create(const float *params, int32_t device, mmas_prior **
     const size_t pb = NPARAM * sizeof(float);
     void **fb[] = {(void **)&p->params, (void **)&p->grad, (void **)&p->adam_m, (void **)&p->adam_v};
     for (void **b : fb) {
-        if ((e = cudaMalloc(b, pb)) != cudaSuccess || (e = cudaMemset(*b, 0, pb)) != cudaSuccess) {
+        if ((e = device_malloc(b, pb)) != cudaSuccess || (e = cudaMemset(*b, 0, pb)) != cudaSuccess) {
             p->errmsg = std::string("cudaMalloc: ") + cudaGetErrorString(e);
             return fail_all(MMAS_ENOMEM);
         }
@@ -494,13 +494,13 @@ mmas_status mmas_prior_create(const float *params, int32_t device, mmas_prior **
     const size_t wsz[5] = {H * FIN, 3 * H * 2 * H, 3 * H * 2 * H, H * H, H * H};
     bf16 **wb[5] = {&p->w0, &p->wl, &p->wlt, &p->wq, &p->wqt};
     for (int i = 0; i < 5; ++i)
-        if ((e = cudaMalloc(wb[i], wsz[i] * sizeof(bf16))) != cudaSuccess) {
+        if ((e = device_malloc(wb[i], wsz[i] * sizeof(bf16))) != cudaSuccess) {
             p->errmsg = std::string("cudaMalloc: ") + cudaGetErrorString(e);
             return fail_all(MMAS_ENOMEM);
         }
-    if ((e = cudaMalloc(&p->err, sizeof(uint32_t))) != cudaSuccess ||
+    if ((e = device_malloc(&p->err, sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMemset(p->err, 0, sizeof(uint32_t))) != cudaSuccess ||
-        (e = cudaMalloc(&p->loss, sizeof(double))) != cudaSuccess) {
+        (e = device_malloc(&p->loss, sizeof(double))) != cudaSuccess) {
         p->errmsg = std::string("cudaMalloc: ") + cudaGetErrorString(e);
         return fail_all(MMAS_ENOMEM);
     }

@@ -11,6 +11,7 @@
 //   wmat  float [n][ld]    choice_info (cl > 0) or 1/choice_info (cl = 0)
 //   cand32 int32 [n][cl]   cand16 uint16 [n][cl]   cwinv float [n][cl]
 //   tours int32 [m][ld]    lens int32 [m]   gb_tour int32 [n]   nbr int2 [n]
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +41,10 @@ struct DeviceGuard {
     }
 };
 
+// Armed by mmas_debug_fail_allocation: device allocations to let through
+// before one fails (-1: none fails).
+std::atomic<int> g_fail_after{-1};
+
 mmas_status fail(mmas_handle *h, mmas_status st, const std::string &msg)
 {
     if (h)
@@ -67,7 +72,7 @@ void free_all(mmas_handle *h)
         if (e) cudaEventDestroy(e);
     void *bufs[] = {h->xy,      h->dist,   h->eb,      h->tau,     h->wmat, h->cwinv,
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
-                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->nnd,
+                    h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->ext_bad, h->nnd,
                     h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -82,7 +87,7 @@ void free_all(mmas_handle *h)
 template <typename T>
 cudaError_t dalloc(T **p, size_t bytes, cudaStream_t stream)
 {
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
+    cudaError_t e = device_malloc(reinterpret_cast<void **>(p), bytes ? bytes : 16);
     if (e == cudaSuccess) e = cudaMemsetAsync(*p, 0, bytes ? bytes : 16, stream);
     return e;
 }
@@ -104,6 +109,9 @@ mmas_status sync_and_check(mmas_handle *h, bool tour = false)
             return fail(h, MMAS_ETIMEOUT, "a shared-memory staging wait on the device timed out");
         if (e & ERR_LS_CAP)
             return fail(h, MMAS_ESTATE, "a 2-opt search exceeded its move cap and stopped early");
+        if (e & ERR_BAD_TOUR)
+            return fail(h, MMAS_ESTATE, "a device-side tour given to mmas_update_device was not a permutation "
+                                        "of 0..n-1 (or its length not positive); that update was skipped");
         return fail(h, MMAS_ESTATE, "the device found no unvisited node during a selection");
     }
     return MMAS_OK;
@@ -244,6 +252,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     CK(h, dalloc(&h->maxd, sizeof(int), h->stream));
     CK(h, dalloc(&h->ext_tour, (size_t)n * sizeof(int32_t), h->stream));
     CK(h, dalloc(&h->ext_len, sizeof(int32_t), h->stream));
+    CK(h, dalloc(&h->ext_bad, sizeof(uint32_t), h->stream));
     CK(h, cudaMallocHost(reinterpret_cast<void **>(&h->h_sc), sizeof(Scalars)));
     CK(h, cudaMallocHost(reinterpret_cast<void **>(&h->h_tour), (size_t)n * sizeof(int32_t)));
     std::memset(h->h_sc, 0, sizeof(Scalars));
@@ -364,6 +373,21 @@ mmas_status check_handle(mmas_handle *h)
 
 void mmas::set_thread_error(const std::string &msg) { tl_error = msg; }
 
+cudaError_t mmas::device_malloc(void **p, size_t bytes)
+{
+    int v = g_fail_after.load();
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v == 0 ? -1 : v - 1)) {
+            if (v == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 mmas_status mmas::validate_colony(const mmas_instance *inst, const mmas_params *params)
 {
     mmas_params p = *params;
@@ -372,6 +396,19 @@ mmas_status mmas::validate_colony(const mmas_instance *inst, const mmas_params *
 }
 
 extern "C" {
+
+void mmas_debug_fail_allocation(int32_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+mmas_status mmas_debug_expire_stage_waits(int32_t device, int32_t on)
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, MMAS_EINVAL, "device ordinal out of range");
+    DeviceGuard g(device);
+    const cudaError_t e = set_stage_wait_expiry(on != 0);
+    if (e != cudaSuccess) return fail(nullptr, MMAS_ECUDA, std::string("set_stage_wait_expiry: ") + cudaGetErrorString(e));
+    return MMAS_OK;
+}
 
 void mmas_default_params(mmas_params *p)
 {
@@ -596,6 +633,7 @@ mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out)
     out->construct_smem = (int32_t)h->cplan.smem;
     out->row_pitch = h->ld;
     out->fallback_scans = (int64_t)s.fallback_scans;
+    out->construct_ants_per_warp = h->cplan.pair ? 2 : 1;
     return MMAS_OK;
 }
 

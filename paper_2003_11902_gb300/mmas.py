@@ -28,7 +28,10 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
+           "mmas_debug_fail_allocation", "mmas_debug_expire_stage_waits",
+           "mmas_shard_best_key", "mmas_shard_tour", "mmas_update_device",
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
+           "mmas_probe_l2_bandwidth",
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
            "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
            "mmas_prior_destroy", "mmas_prior_last_error", "mmas_prior_apply_weighted",
@@ -63,7 +66,7 @@ class mmas_stats_t(C.Structure):
                 ("tau_max", C.c_float), ("construct_grid", C.c_int32),
                 ("construct_block", C.c_int32), ("construct_staged", C.c_int32),
                 ("construct_smem", C.c_int32), ("row_pitch", C.c_int32),
-                ("fallback_scans", C.c_int64)]
+                ("fallback_scans", C.c_int64), ("construct_ants_per_warp", C.c_int32)]
 
 
 class MMASError(RuntimeError):
@@ -103,12 +106,18 @@ def load(path: str = LIB_PATH):
             "mmas_get_setup": (C.c_int, [H, P(i32), P(f32), P(i32), P(i64)]),
             "mmas_set_iteration": (C.c_int, [H, i32]),
             "mmas_stats": (C.c_int, [H, P(mmas_stats_t)]),
+            "mmas_debug_fail_allocation": (None, [i32]),
+            "mmas_shard_best_key": (C.c_int, [H, C.c_void_p]),
+            "mmas_shard_tour": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+            "mmas_update_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+            "mmas_debug_expire_stage_waits": (C.c_int, [i32, i32]),
             "mmas_synchronize": (C.c_int, [H]),
             "mmas_enable_phase_timing": (C.c_int, [H, i32]),
             "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
             "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
             "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
+            "mmas_probe_l2_bandwidth": (C.c_int, [i32, i64, P(C.c_double)]),
             "mmas_gemm_bf16": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, C.c_void_p,
                                         i32, i32, i32, i32, i32, C.c_void_p]),
             "mmas_prior_create": (C.c_int, [P(f32), i32, P(H)]),
@@ -274,6 +283,18 @@ def mmas_stats(h) -> dict:
     return {f: getattr(s, f) for f, _ in mmas_stats_t._fields_}
 
 
+def mmas_debug_fail_allocation(after: int):
+    """Arm a simulated device out-of-memory `after` allocations from now
+    (-1 disarms); see include/mmas.h."""
+    load().mmas_debug_fail_allocation(int(after))
+
+
+def mmas_debug_expire_stage_waits(device: int, on: bool):
+    """Make the construction's staging waits on `device` run out (testing aid;
+    see include/mmas.h)."""
+    _check(None, load().mmas_debug_expire_stage_waits(int(device), int(bool(on))))
+
+
 def mmas_synchronize(h):
     _check(h, load().mmas_synchronize(h))
 
@@ -299,6 +320,11 @@ def mmas_score_tours_noalloc(d_tours: int, m: int, n: int, pitch: int, d_xy: int
         stream = _torch_stream()
     _check(None, load().mmas_score_tours_noalloc(d_tours, m, n, pitch, d_xy, d_lens, d_best,
                                                   stream))
+
+
+def _dptr(x) -> int:
+    """A device address: an int, or a tensor's data_ptr()."""
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
 
 
 # ------------------------------------------------------------------- Colony
@@ -381,6 +407,21 @@ class Colony:
     def stats(self) -> dict:
         return mmas_stats(self._h)
 
+    def shard_best_key(self, key):
+        """Enqueue: the device int64 `key` (a tensor or an address) = (length
+        << 32 | global ant) of the shortest tour of the last construction."""
+        _check(self._h, load().mmas_shard_best_key(self._h, _dptr(key)))
+
+    def shard_tour(self, key, tour):
+        """Enqueue: device int32[n] `tour` = the key's tour if this shard built
+        it, else zeros."""
+        _check(self._h, load().mmas_shard_tour(self._h, _dptr(key), _dptr(tour)))
+
+    def update_device(self, tour, key):
+        """Enqueue the update with a device-side tour and the key's length,
+        then advance the iteration index."""
+        _check(self._h, load().mmas_update_device(self._h, _dptr(tour), _dptr(key)))
+
     def synchronize(self):
         mmas_synchronize(self._h)
 
@@ -396,6 +437,14 @@ def mmas_probe_draw_rate(device: int = 0, ms: float = 50.0) -> float:
     occupancy (a measurement aid; see include/mmas.h)."""
     v = C.c_double()
     _check(None, load().mmas_probe_draw_rate(device, ms, C.byref(v)))
+    return v.value
+
+
+def mmas_probe_l2_bandwidth(device: int = 0, nbytes: int = 32 << 20) -> float:
+    """L2 read bandwidth in GB/s over an L2-resident buffer (a measurement aid;
+    see include/mmas.h)."""
+    v = C.c_double()
+    _check(None, load().mmas_probe_l2_bandwidth(device, int(nbytes), C.byref(v)))
     return v.value
 
 

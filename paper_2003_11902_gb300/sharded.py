@@ -11,16 +11,22 @@ keys the draws by the global ant index).  The iteration's single exchange is:
   2. a broadcast of that tour (n ids) from the rank that owns the ant.
 
 Every rank then applies the same deterministic update to its replica of the
-pheromone (``mmas_update``), so the replicas stay identical and the run equals
-the single-colony run whatever the number of ranks.  The exchange is 8 + 4n
-bytes per iteration.
+pheromone, so the replicas stay identical and the run equals the single-colony
+run whatever the number of ranks.  The exchange is 8 + 4n bytes per iteration.
+
+``sharded_iteration_device`` keeps the whole exchange on the GPU: the library
+writes the packed key and the owner's tour into device buffers
+(mmas_shard_best_key, mmas_shard_tour), the ranks all-reduce them (MIN, then
+SUM of a buffer that only the owner fills), and mmas_update_device applies the
+update from the device tour, with no host copy.  ``sharded_iteration`` is the
+host-side form (tours copied out, argmin on the host, tour copied back).
 """
 from __future__ import annotations
 
 import numpy as np
 
 __all__ = ["shard_range", "owner_of", "pack", "unpack", "exchange_iteration_best",
-           "sharded_iteration"]
+           "sharded_iteration", "sharded_iteration_device", "nccl_reducers"]
 
 
 def shard_range(m: int, rank: int, world: int):
@@ -72,6 +78,35 @@ def exchange_iteration_best(lens, tours, offset: int, m: int, group=None, device
     dist.broadcast(buf, src=dist.get_global_rank(group, owner) if group is not None else owner,
                    group=group)
     return length, ant, buf.cpu().numpy()
+
+
+def nccl_reducers(group=None):
+    """The exchange's two all-reduces for torch.distributed (NCCL between GPUs,
+    gloo on host tensors): MIN of the key, SUM of the tour buffer, in place."""
+    import torch.distributed as dist
+
+    def rmin(t):
+        dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+
+    def rsum(t):
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return rmin, rsum
+
+
+def sharded_iteration_device(colony, key, tour, reduce_min, reduce_sum):
+    """One iteration of a sharded colony with the exchange on device buffers:
+    construct this shard's ants; key (1 int64) = its shortest tour's packed
+    (length, global ant); all-reduce MIN; tour (n int32) = that ant's tour if
+    this shard owns it, else zeros; all-reduce SUM; the common update, which
+    advances the iteration.  Only key and tour cross ranks: 8 + 4n bytes.
+    ``colony`` is a ``Colony`` built with this rank's m and ant_offset (or any
+    object with the same four methods); nothing is copied to the host."""
+    colony.construct()
+    colony.shard_best_key(key)
+    reduce_min(key)
+    colony.shard_tour(key, tour)
+    reduce_sum(tour)
+    colony.update_device(tour, key)
 
 
 def sharded_iteration(colony, it: int, m_total: int, group=None, device="cpu"):

@@ -11,13 +11,20 @@ import bench
 
 
 def test_algorithmic_construct_bytes():
-    # cl > 0: per step cl x (2 B id + 4 B reciprocal weight), plus 4 B of tour
-    # per node; at n = m = 1000, cl = 32: 195.8 MB
+    # the method's logical reads: per step each candidate's 4-byte weight and
+    # 4-byte id, 256 B at cl = 32 -- 255.7 MB a launch at n = m = 1000 (the
+    # figure of the survey's n = 1000 row: 256 B per step)
     w = bench.WORKLOADS["uniform-n1000-cl32"]
-    assert bench.algorithmic_construct_bytes(w) == 1000 * (999 * 32 * 6 + 4 * 1000) == 195_808_000
+    assert bench.algorithmic_construct_bytes(w) == 1000 * 999 * 32 * 8 == 255_744_000
+    # the clustered workload: 128 B per step, 3,800 - 1 steps per ant, 1000 ants
+    w = bench.WORKLOADS["clustered-n3800-cl16-2opt"]
+    assert bench.algorithmic_construct_bytes(w) == 1000 * 3799 * 16 * 8
     # whole rows: the unvisited weights of every step, 4 B each: n(n-1)/2 per ant
     w = bench.WORKLOADS["uniform-n200-fullrow"]
-    assert bench.algorithmic_construct_bytes(w) == 200 * (4 * (200 * 199 // 2) + 4 * 200)
+    assert bench.algorithmic_construct_bytes(w) == 200 * (4 * (200 * 199 // 2))
+    # as stored: 16-bit ids and 4-byte reciprocal weights, plus the tour entries
+    w = bench.WORKLOADS["uniform-n1000-cl32"]
+    assert bench.stored_construct_bytes(w) == 1000 * (999 * 32 * 6 + 4 * 1000) == 195_808_000
 
 
 def test_every_stored_lstar_exists():

@@ -200,6 +200,60 @@ def test_greedy_fallback_on_a_converged_trail_matches_oracle(n, cl, kind):
     g.close()
 
 
+@pytest.mark.parametrize("n,cl,kind,m,fallback,trail", [
+    (4200, 16, "clustered", 1901, 0, "deposits"),
+    (5000, 8, "uniform", 1902, 1, "deposits"),
+    (4500, 12, "uniform", 1903, 0, "converged"),
+])
+def test_two_ants_per_warp_match_oracle(n, cl, kind, m, fallback, trail):
+    """Many ants, short lists and shared-memory tabus: each half of a warp
+    builds one tour (with an odd count the last warp's second half only
+    repeats the first half's ant).  After deposits on long random tours, or on
+    a converged-looking trail, fallbacks of every kind run in either half;
+    sampled ants, the last one included, match the oracle pick for pick."""
+    xy = I.clustered(n, 80 + n) if kind == "clustered" else I.uniform(n, 80 + n)
+    g, o = _pair(xy=xy, m=m, cl=cl, rho=0.05, seed=11, fallback=fallback)
+    d = o.state()["d"]
+    if trail == "deposits":
+        for r in range(12):
+            tour = I.random_permutation(n, 900 + r) if r % 3 else O.nn_tour(d)[1]
+            length = int(O.tour_length(d, tour))
+            g.update(tour, length)
+            o.update(tour, length)
+        it = o.iteration
+    else:
+        tmax, tmin = np.float32(1e-3), np.float32(1e-7)
+        tau = np.full((n, n), tmin, np.float32)
+        t = O.nn_tour(d)[1]
+        tau[t, np.roll(t, -1)] = tmax
+        tau[np.roll(t, -1), t] = tmax
+        rng = np.random.default_rng(n)
+        for _ in range(3):
+            j = rng.permutation(n)
+            lv = (tmin * 10.0 ** rng.uniform(1, 4, n)).astype(np.float32)
+            tau[np.arange(n), j] = np.maximum(tau[np.arange(n), j], lv)
+            tau[j, np.arange(n)] = tau[np.arange(n), j]
+        np.fill_diagonal(tau, tmax)
+        g.set_pheromone(tau, tmin, tmax)
+        g.set_pheromone(tau, tmin, tmax)
+        o.set_pheromone(tau, tmin, tmax)
+        it = 3
+    g.set_iteration(it)
+    g.construct()
+    tours, lens = g.tours()
+    st = g.stats()
+    assert st["construct_ants_per_warp"] == 2
+    assert np.array_equal(np.sort(tours, axis=1), np.broadcast_to(np.arange(n, dtype=np.int32), (m, n)))
+    sample = list(range(0, m, 60)) + [m - 2, m - 1]
+    kinds = [check_ant(o, it, k, tours[k], lens[k]) for k in sample]
+    near = kinds.count("near_tie")
+    print(f"n={n} cl={cl} m={m} fallback={fallback} {trail}: {st['fallback_steps']} fallbacks "
+          f"({st['fallback_scans']} row scans), {near} near-tie divergences in {len(sample)} ants")
+    assert st["fallback_steps"] > m
+    assert near <= max(1, len(sample) // 50)
+    g.close()
+
+
 def test_lockstep_iterations_match_oracle():
     """Whole-run parity: as long as every pick agrees, tours, lengths, limits,
     best tour and pheromone agree after every iteration."""
