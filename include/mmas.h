@@ -67,8 +67,9 @@ typedef struct {
  *   p_best   the Stuetzle-Hoos parameter fixing tau_min/tau_max, 0 < p_best < 1
  *                                                                   (0.01)
  *   cl       candidate-list length: 0 samples the whole row (Eq. (1) over all
- *            unvisited nodes); 1..32 samples the cl nearest nodes (Sec. 4.3),
- *            cl < n                                                (32)
+ *            unvisited nodes); 1..64 samples the cl nearest nodes (Sec. 4.3),
+ *            cl < n.  Up to 32 one warp lane scores one candidate; above 32
+ *            each lane scores two (slots l and l + 32).  ls needs cl <= 32 (32)
  *   seed     key of the counter-based generator (Philox4x32-10)    (1)
  *   deposit  0: deposit on the iteration best, 1: on the global best (0)
  *   fallback when every candidate of the current node is visited:
@@ -146,8 +147,6 @@ typedef struct {
     int32_t row_pitch;         /* elements per row of the n x n device matrices      */
     int64_t fallback_scans;    /* of the fallback steps, those that scanned the whole
                                   row (the rest were decided on the reach list)      */
-    int32_t construct_ants_per_warp; /* 1, or 2 when each half of a warp builds a tour
-                                  (candidate lists of at most 16, n > 4096, many ants) */
 } mmas_stats_t;
 
 /* Fill *p with the defaults listed at mmas_params (m = 0 means "m = n"). */
@@ -488,7 +487,8 @@ const char *mmas_batch_last_error(const mmas_batch *b);
  *            permutation of 0..n-1)
  *   m        1 <= m <= MMAS_NOALLOC_MAX_ANTS
  *   n        3 <= n <= 65535;  pitch >= n (elements per row)
- *   d_xy     device, n x 2 int32 coordinates, |x|, |y| < 2^30
+ *   d_xy     device, n x 2 int32 coordinates, |x|, |y| < 2^30, 8-byte aligned
+ *            (the other buffers 4-byte aligned)
  *   d_lens   device, m int32 (out): tour lengths; n * max(d) must be < 2^31
  *   d_best   device, 2 int32 (out): {shortest length, lowest ant reaching it}
  *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream)
@@ -496,7 +496,10 @@ const char *mmas_batch_last_error(const mmas_batch *b);
  * Errors: EINVAL for a NULL buffer or a size out of range (checked before any
  * GPU work, message in mmas_last_error(NULL)); ECUDA if a CUDA call fails.
  * The first call on each device looks up the scratch's device address with
- * that device current; make that first call before any stream capture.
+ * that device current and keeps it for the life of the process; make that
+ * first call before any stream capture.  cudaDeviceReset unloads the library's
+ * device code and so invalidates the kept address: after resetting a device,
+ * do not call this entry point on it again in the same process.
  * Every call shares the scratch and a call leaves it holding its own partial
  * results, so calls whose GPU work may overlap (e.g. on different streams
  * with no ordering between them) race and must be serialised by the caller. */

@@ -557,225 +557,6 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
     }
 }
 
-// ---------------------------------------------------------------------------
-// Two ants per warp: candidate lists of at most 16 entries with the tabu in
-// shared memory.  Lanes 0-15 build one ant's tour and lanes 16-31 another's in
-// the same instructions: lane l scores slot l & 15 of its ant's list and each
-// half reduces its keys under its own mask.  Draws, picks, fallbacks and tours
-// are exactly those of one ant per warp (the same counters, the same ties).
-// ---------------------------------------------------------------------------
-
-// Score slot `slot` of row cur for the enabled half; the half's largest key in
-// mx (0: no unvisited candidate) and its node (ties -> lower id).
-template <bool PART>
-__device__ __forceinline__ uint32_t pair_pick(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                              const uint32_t *tw, int cur, int slot, unsigned hmask,
-                                              bool en, float lg, uint32_t &mx)
-{
-    const bool act = en && slot < a.cl;
-    uint32_t v;
-    float wi;
-    cand_load<PART>(a, cc, cw, cur, act ? cur * a.cl + slot : 0, v, wi);
-    const uint32_t word = tw[v >> 5];
-    const bool ok = act && !((word >> (v & 31)) & 1u);
-    const uint32_t k = ok ? neg_key(__fmul_rn(lg, wi)) : 0u;
-    mx = __reduce_max_sync(hmask, k);
-    return __reduce_min_sync(hmask, k == mx ? v : 0xFFFFFFFFu);
-}
-
-// Per-lane view of the two ants of a warp.
-struct PairCtx {
-    int lane, half, slot;  // slot = lane & 15
-    unsigned hmask;        // this half's lanes
-    uint32_t *tbase;       // the warp's tabus: half h at tbase + h nw
-    uint32_t *tw;          // this half's tabu
-    int nw;
-    int ant;               // this half's ant (global index, keys the draws)
-    bool wr;               // this half's ant is real (writes its tour and counts)
-};
-
-// The greedy / sampled fallback of half h's ant, run by the whole warp; every
-// lane returns the node, and the half's lanes count it.
-__device__ __forceinline__ int pair_fallback(const ConstructArgs &a, const PairCtx &c, int h, int cur, int t,
-                                             uint32_t it, unsigned long long &fbn)
-{
-    const int hc = __shfl_sync(FULL, cur, 16 * h);
-    const int hant = __shfl_sync(FULL, c.ant, 16 * h);
-    Tabu<0> tb;
-    tb.w = c.tbase + (size_t)h * c.nw;
-    tb.nw = c.nw;
-    const int r = cand_fallback<0>(a.wmat + (size_t)hc * a.ld, a.n, tb, c.lane, a.fallback, (uint32_t)t,
-                                   (uint32_t)hant, it, a.key0, a.key1, &a.sc->err, hc,
-                                   a.xlw + (size_t)hc * a.xe, a.xlb + hc,
-                                   a.xxw + (size_t)hc * REACH_EXTRA, a.xxn + hc, a.xe);
-    unsigned long long dummy = 0;
-    const int node = count_fallback(r, c.half == h ? fbn : dummy);
-    return node;
-}
-
-// Half h takes node `node` as its step-t entry: mark, window slot, cur.
-__device__ __forceinline__ void pair_take(const PairCtx &c, int h, int node, int t, int &cur, int &twin)
-{
-    if (c.half == h) {
-        if (c.slot == 0) c.tw[node >> 5] |= 1u << (node & 31);
-        twin = (c.slot == (t & 15)) ? node : twin;
-        cur = node;
-    }
-    __syncwarp();
-}
-
-// Step t for half h alone (the other half idles), with its fallback.
-template <bool PART>
-__device__ __forceinline__ void pair_step_half(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                               const PairCtx &c, int h, int t, float lg, uint32_t it,
-                                               int &cur, int &twin, unsigned long long &fbn)
-{
-    uint32_t mx;
-    const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, c.half == h, lg, mx);
-    const uint32_t hmx = __shfl_sync(FULL, mx, 16 * h);
-    const int node = hmx != 0u ? (int)__shfl_sync(FULL, nxt, 16 * h) : pair_fallback(a, c, h, cur, t, it, fbn);
-    pair_take(c, h, node, t, cur, twin);
-}
-
-// Step t for both halves one after the other where a fallback is needed.
-template <bool PART>
-__device__ __forceinline__ void pair_step_both(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                               const PairCtx &c, int t, float lg, uint32_t it, int &cur,
-                                               int &twin, unsigned long long &fbn)
-{
-    uint32_t mx;
-    const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, true, lg, mx);
-    const unsigned frozen = __ballot_sync(FULL, mx == 0u);
-    if (c.slot == 0 && mx != 0u) c.tw[nxt >> 5] |= 1u << (nxt & 31);
-    twin = (mx != 0u && c.slot == (t & 15)) ? (int)nxt : twin;
-    cur = mx != 0u ? (int)nxt : cur;
-    __syncwarp();
-    for (int h = 0; h < 2; ++h)
-        if ((frozen >> (16 * h)) & 0xFFFFu) pair_take(c, h, pair_fallback(a, c, h, cur, t, it, fbn), t, cur, twin);
-}
-
-// Store half-window w (steps 16w .. t_end) of this lane's ant: slot s holds
-// entry 16w + s.
-__device__ __forceinline__ void pair_store(const PairCtx &c, int32_t *trow, int w, int t_end, int twin)
-{
-    if (c.wr && c.slot <= t_end - 16 * w) trow[16 * w + c.slot] = twin;
-}
-
-// The generator call of group g + 1 spread over the four steps of group g.
-__device__ __forceinline__ void pair_gen(const ConstructArgs &a, uint4 &nx, float (&nl)[4], int j)
-{
-    if (j == 0) philox_rounds_rk<0, 4>(nx, a.rk0, a.rk1);
-    if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
-    if (j == 2) {
-        philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
-        nl[0] = log2f(unit_open(nx.x));
-        nl[1] = log2f(unit_open(nx.y));
-    }
-    if (j == 3) {
-        nl[2] = log2f(unit_open(nx.z));
-        nl[3] = log2f(unit_open(nx.w));
-    }
-}
-
-// Group g (steps 4g .. 4g+3) with checks: steps t = 0 and t >= n are skipped
-// and windows stored as they complete (first and last groups).
-template <bool PART>
-__device__ __forceinline__ void pair_group_checked(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                                   const PairCtx &c, int32_t *trow, uint32_t it, int g,
-                                                   float (&lg)[4], int &cur, int &twin,
-                                                   unsigned long long &fbn)
-{
-    uint4 nx = make_uint4((uint32_t)c.slot, (uint32_t)(g + 1), (uint32_t)c.ant, it);
-    float nl[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        pair_gen(a, nx, nl, j);
-        const int t = 4 * g + j;
-        if (t == 0 || t >= a.n) continue;
-        pair_step_both<PART>(a, cc, cw, c, t, lg[j], it, cur, twin, fbn);
-        if ((t & 15) == 15 || t == a.n - 1) pair_store(c, trow, t >> 4, t, twin);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
-}
-
-// A full group inside the tour: a half whose candidates are all visited
-// freezes for the rest of the group; afterwards each frozen half takes its
-// fallback and its remaining steps alone.  Equal to four checked steps.
-template <bool PART>
-__device__ __forceinline__ void pair_group(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                           const PairCtx &c, uint32_t it, int g, float (&lg)[4], int &cur,
-                                           int &twin, unsigned long long &fbn)
-{
-    uint4 nx = make_uint4((uint32_t)c.slot, (uint32_t)(g + 1), (uint32_t)c.ant, it);
-    float nl[4];
-    const int tb16 = (4 * g) & 15;
-    bool live = true;  // uniform within the half
-    int jfail = 4;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        pair_gen(a, nx, nl, j);
-        uint32_t mx;
-        const uint32_t nxt = pair_pick<PART>(a, cc, cw, c.tw, cur, c.slot, c.hmask, true, lg[j], mx);
-        jfail = (live && mx == 0u) ? j : jfail;
-        live = live && mx != 0u;
-        if (c.slot == 0 && live) c.tw[nxt >> 5] |= 1u << (nxt & 31);
-        twin = (live && c.slot == tb16 + j) ? (int)nxt : twin;
-        cur = live ? (int)nxt : cur;
-        __syncwarp();
-    }
-    const unsigned frozen = __ballot_sync(FULL, jfail < 4);
-    if (__builtin_expect(frozen != 0u, 0)) {
-        for (int h = 0; h < 2; ++h) {
-            if (!((frozen >> (16 * h)) & 0xFFFFu)) continue;
-            const int hj = __shfl_sync(FULL, jfail, 16 * h);
-            pair_take(c, h, pair_fallback(a, c, h, cur, 4 * g + hj, it, fbn), 4 * g + hj, cur, twin);
-            for (int j = hj + 1; j < 4; ++j) pair_step_half<PART>(a, cc, cw, c, h, 4 * g + j, lg[j], it, cur, twin, fbn);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) lg[j] = nl[j];
-}
-
-// The tours of a pair of ants (this lane's half builds c.ant's).
-template <bool PART>
-__device__ __forceinline__ void build_tour_pair(const ConstructArgs &a, const uint16_t *cc, const float *cw,
-                                                PairCtx &c, uint32_t it, int32_t *trow)
-{
-    uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)c.ant, it);
-    philox_rounds<0, 10>(s4, a.key0, a.key1);
-    const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
-    for (int q = c.slot; q < c.nw; q += 16) c.tw[q] = 0u;
-    __syncwarp();
-    if (c.slot == 0) c.tw[start >> 5] |= 1u << (start & 31);
-    __syncwarp();
-    int cur = start, twin = start;
-    unsigned long long fbn = 0;
-    float lg[4];
-    {
-        uint4 r = make_uint4((uint32_t)c.slot, 0u, (uint32_t)c.ant, it);
-        philox_rounds<0, 10>(r, a.key0, a.key1);
-        lg[0] = 0.0f;  // step 0 is the start node
-        lg[1] = log2f(unit_open(r.y));
-        lg[2] = log2f(unit_open(r.z));
-        lg[3] = log2f(unit_open(r.w));
-    }
-    pair_group_checked<PART>(a, cc, cw, c, trow, it, 0, lg, cur, twin, fbn);
-    int g = 1;
-    for (; 4 * g + 3 <= a.n - 1; ++g) {
-        pair_group<PART>(a, cc, cw, c, it, g, lg, cur, twin, fbn);
-        if ((g & 3) == 3) pair_store(c, trow, g >> 2, 4 * g + 3, twin);
-    }
-    if (4 * g <= a.n - 1)
-        pair_group_checked<PART>(a, cc, cw, c, trow, it, g, lg, cur, twin, fbn);
-    else if (g > 1 && ((g - 1) & 3) != 3)
-        pair_store(c, trow, (g - 1) >> 2, a.n - 1, twin);  // the last full group ended it
-    if (c.wr && c.slot == 0 && fbn) {
-        atomicAdd(&a.sc->fallback_steps, fbn & 0xFFFFFFFFull);
-        if (fbn >> 32) atomicAdd(&a.sc->fallback_scans, fbn >> 32);
-    }
-}
-
 // Stage `bytes_w` bytes of weights and `bytes_c` of ids into shared memory
 // with the bulk-copy engine (thread 0 issues, every thread waits on the
 // mbarrier, bounded).  Returns false on a timeout, after which the CTA must
@@ -814,9 +595,12 @@ __device__ __forceinline__ bool stage_table(unsigned char *s_w, const void *src_
 }
 
 // STAGED: 0 the table is read from global memory; 1 it is staged whole; 2
-// its first a.stage_rows rows are staged (candidate-list mode).
-template <int MODE, int STAGED, int TW>
-__global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int cons_warps)
+// its first a.stage_rows rows are staged (candidate-list mode).  MAXT: threads
+// a CTA may have -- 384 (12 warps, registers for the four-step groups) or,
+// for tables mostly too large to stage, 1024 (32 warps with fewer registers
+// each: the dependent row reads from L2 are hidden by more ants per SM).
+template <int MODE, int STAGED, int TW, int MAXT = 384>
+__global__ void __launch_bounds__(MAXT, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -855,50 +639,85 @@ __global__ void __launch_bounds__(384, 1) k_construct(const ConstructArgs a, int
         build_tour<MODE, TW, STAGED == 2>(a, cc, cw, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
 }
 
-// Two ants per warp (candidate lists of at most 16, tabu in shared memory).
-// STAGED as for k_construct.  Warp w of the grid builds ants 2w and 2w + 1 of
-// each round; with an odd count the second half of the last warp repeats the
-// first half's ant without writing it.
-template <int STAGED>
-__global__ void __launch_bounds__(384, 1) k_construct_pair(const ConstructArgs a, int cons_warps)
+// Candidate lists longer than a warp (32 < cl <= 64): lane l scores slots l
+// and l + 32 of the current list (its two draws come from the slots' own
+// counters), keeps the better of the two (ties -> lower id) and the warp
+// reduces as for one slot a lane.  The table (n x cl x 6 B) is read from L2.
+template <int TW>
+__device__ __forceinline__ int cand_step2(const ConstructArgs &a, const Tabu<TW> &tb, int lane, int cur,
+                                          float lg0, float lg1, int t, int ant, uint32_t it,
+                                          unsigned long long &fbn)
+{
+    const size_t base = (size_t)cur * a.cl;
+    const int s1 = lane + 32;
+    const bool act1 = s1 < a.cl;
+    const uint32_t v0 = a.cand16[base + lane];
+    const float w0 = a.cwinv[base + lane];
+    const uint32_t v1 = act1 ? a.cand16[base + s1] : v0;
+    const float w1 = act1 ? a.cwinv[base + s1] : w0;
+    const uint32_t word0 = tb.word_of((int)v0);  // every lane calls both
+    const uint32_t word1 = tb.word_of((int)v1);
+    const uint32_t k0 = !((word0 >> (v0 & 31)) & 1u) ? neg_key(__fmul_rn(lg0, w0)) : 0u;
+    const uint32_t k1 = (act1 && !((word1 >> (v1 & 31)) & 1u)) ? neg_key(__fmul_rn(lg1, w1)) : 0u;
+    const bool second = k1 > k0 || (k1 == k0 && k1 != 0u && v1 < v0);
+    const uint32_t k = second ? k1 : k0, v = second ? v1 : v0;
+    const uint32_t mx = __reduce_max_sync(FULL, k);
+    if (__builtin_expect(mx != 0u, 1)) return (int)__reduce_min_sync(FULL, k == mx ? v : 0xFFFFFFFFu);
+    return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
+                                            (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
+                                            a.xlw + (size_t)cur * a.xe, a.xlb + cur,
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+                          fbn);
+}
+
+template <int TW>
+__device__ __forceinline__ void build_tour_long(const ConstructArgs &a, Tabu<TW> &tb, int lane, int ant,
+                                                uint32_t it, int32_t *trow)
+{
+    uint4 s4 = make_uint4(0xFFFFFFFFu, 0u, (uint32_t)ant, it);
+    philox_rounds<0, 10>(s4, a.key0, a.key1);
+    const int start = (int)(((unsigned long long)s4.x * (unsigned)a.n) >> 32);
+    tb.clear(lane);
+    tb.mark(lane, start);
+    int cur = start, twin = start;
+    unsigned long long fbn = 0;
+    uint4 r0 = make_uint4(0u, 0u, 0u, 0u), r1 = r0;
+    for (int t = 1; t < a.n; ++t) {
+        if (t == 1 || (t & 3) == 0) {  // the words of slots lane and lane + 32 for group t/4
+            r0 = make_uint4((uint32_t)lane, (uint32_t)(t >> 2), (uint32_t)ant, it);
+            r1 = make_uint4((uint32_t)(lane + 32), (uint32_t)(t >> 2), (uint32_t)ant, it);
+            philox_rounds_rk<0, 10>(r0, a.rk0, a.rk1);
+            philox_rounds_rk<0, 10>(r1, a.rk0, a.rk1);
+        }
+        const float lg0 = log2f(unit_open(pick_word(r0, t & 3)));
+        const float lg1 = log2f(unit_open(pick_word(r1, t & 3)));
+        const int next = cand_step2<TW>(a, tb, lane, cur, lg0, lg1, t, ant, it, fbn);
+        tb.mark(lane, next);
+        twin = (lane == (t & 31)) ? next : twin;
+        if ((t & 31) == 31 || t == a.n - 1) store_window(trow, lane, t >> 5, t, twin);
+        cur = next;
+    }
+    if (lane == 0 && fbn) {
+        atomicAdd(&a.sc->fallback_steps, fbn & 0xFFFFFFFFull);
+        if (fbn >> 32) atomicAdd(&a.sc->fallback_scans, fbn >> 32);
+    }
+}
+
+// One ant per warp, four warps per CTA, for 32 < cl <= 64.
+template <int TW>
+__global__ void __launch_bounds__(128) k_construct_long(const ConstructArgs a, int cons_warps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t it = (uint32_t)a.iter[0];
-    const float *cw = a.cwinv;
-    const uint16_t *cc = a.cand16;
-    size_t off = 0;
-    if constexpr (STAGED != 0) {
-        unsigned char *s_w = smem;
-        off = a.stage_w_bytes;
-        unsigned char *s_c = smem + off;
-        off += a.stage_c_bytes;
-        uint64_t *bar = reinterpret_cast<uint64_t *>(smem + off);
-        off += 16;
-        if (threadIdx.x == 0) mbar_init(bar, 1);
-        __syncthreads();
-        if (!stage_table(s_w, cw, a.stage_w_bytes, s_c, a.cand16, a.stage_c_bytes, bar, 0, &a.sc->err))
-            return;
-        cw = reinterpret_cast<const float *>(s_w);
-        cc = reinterpret_cast<const uint16_t *>(s_c);
-    }
-    PairCtx c;
-    c.lane = lane;
-    c.half = lane >> 4;
-    c.slot = lane & 15;
-    c.hmask = c.half ? 0xFFFF0000u : 0x0000FFFFu;
-    c.nw = (a.n + 31) >> 5;
-    c.tbase = reinterpret_cast<uint32_t *>(smem + off) + (size_t)warp * 2 * c.nw;
-    c.tw = c.tbase + (size_t)c.half * c.nw;
-    const int stride = 2 * gridDim.x * cons_warps;
+    Tabu<TW> tb;
+    tb.nw = (a.n + 31) >> 5;
+    if constexpr (TW == 0) tb.w = reinterpret_cast<uint32_t *>(smem) + (size_t)warp * tb.nw;
+    const int stride = gridDim.x * cons_warps;
     const int ant_end = a.ant_offset + a.m;
     int32_t *const tours_g = a.tours - (size_t)a.ant_offset * a.ld;
-    for (int a0 = a.ant_offset + 2 * (blockIdx.x * cons_warps + warp); a0 < ant_end; a0 += stride) {
-        const int mine = a0 + c.half;
-        c.wr = mine < ant_end;
-        c.ant = c.wr ? mine : a0;
-        build_tour_pair<STAGED == 2>(a, cc, cw, c, it, tours_g + (size_t)c.ant * a.ld);
-    }
+    for (int ant = a.ant_offset + blockIdx.x * cons_warps + warp; ant < ant_end; ant += stride)
+        build_tour_long<TW>(a, tb, lane, ant, it, tours_g + (size_t)ant * a.ld);
 }
 
 // Batched construction: one persistent launch builds every ant of
@@ -1286,9 +1105,16 @@ KernelFn pick_kernel(int mode, int staged, int tw)
     return mode == CAND ? cand[staged][ti] : rowk[staged ? 1 : 0][ti];
 }
 
-KernelFn pick_kernel_pair(int staged)
+// the 32-warp form, tabus in shared memory: staged rows (2) or none (0)
+KernelFn pick_kernel_wide(int staged)
 {
-    return staged == 1 ? k_construct_pair<1> : (staged == 2 ? k_construct_pair<2> : k_construct_pair<0>);
+    return staged == 2 ? k_construct<CAND, 2, 0, 1024> : k_construct<CAND, 0, 0, 1024>;
+}
+
+KernelFn pick_kernel_long(int tw)
+{
+    return tw == 1 ? k_construct_long<1>
+                   : (tw == 2 ? k_construct_long<2> : (tw == 4 ? k_construct_long<4> : k_construct_long<0>));
 }
 
 // whole-row variants: (sel, ct) != (0, 0); TW 1 (n <= 1024) or 0 for the bitmask
@@ -1317,20 +1143,38 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const bool var = row && (a.sel != 0 || a.ct != 0);
     const int nw = (a.n + 31) / 32;
     plan->tw = var ? (a.n <= 1024 ? 1 : 0) : tabu_words(a.n);
-    // two ants per warp: short candidate lists (half a warp scores one list),
-    // shared-memory tabus, and more ants than one-ant warps could carry
-    plan->pair = !row && a.cl <= 16 && plan->tw == 0 && a.m > 12 * num_sms;
-    const int per_ants = plan->pair ? 2 : 1;  // ants a warp builds at once
+    plan->longl = !row && a.cl > 32;
+    if (plan->longl) {  // 32 < cl <= 64: two slots a lane, rows from L2
+        plan->wide = 0;
+        plan->staged = 0;
+        plan->stage_rows = 0;
+        plan->cons_warps = 4;
+        plan->gen_warps = 0;
+        plan->grid = (a.m + 3) / 4;
+        plan->smem = plan->tw ? 0 : (size_t)4 * nw * sizeof(uint32_t);
+        return cudaFuncSetAttribute(reinterpret_cast<const void *>(pick_kernel_long(plan->tw)),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+    }
+    // most rows of the candidate table unstageable (under a quarter of it fits
+    // beside the tabus of 12 warps): 32 warps per CTA (MAXT = 1024), which
+    // stage the rows that still fit beside their tabus
+    plan->wide = 0;
+    if (!row && !var && plan->tw == 0) {
+        const size_t tabus12 = (size_t)12 * nw * sizeof(uint32_t);
+        const size_t room = smem_optin > 16 + tabus12 ? smem_optin - 16 - tabus12 : 0;
+        plan->wide = room / ((size_t)a.cl * 6) * 4 < (size_t)a.n && a.m > 12 * num_sms;
+    }
+    const int max_warps = plan->wide ? 32 : 12;
     // per-warp shared memory besides the table: the compact list, or the tabu
-    // bitmasks when they do not live in registers
+    // bitmask when it does not live in registers
     const size_t per_warp = (var && a.ct) ? (((size_t)a.n * 2 + 15) & ~size_t(15))
-                                          : (plan->tw ? 0 : (size_t)per_ants * nw * sizeof(uint32_t));
+                                          : (plan->tw ? 0 : (size_t)nw * sizeof(uint32_t));
     const size_t table = row ? (size_t)a.n * a.ld * sizeof(float)
                              : (size_t)a.stage_w_bytes + a.stage_c_bytes;
     // staged: one CTA per SM (the table fills its shared memory) carrying
-    // ceil(m / #SMs) ants, at most 12 warps; warps loop over further ants
-    int w = (a.m + per_ants * num_sms - 1) / (per_ants * num_sms);
-    w = w < 1 ? 1 : (w > 12 ? 12 : w);
+    // ceil(m / #SMs) ants, at most max_warps warps; warps loop over further ants
+    int w = (a.m + num_sms - 1) / num_sms;
+    w = w < 1 ? 1 : (w > max_warps ? max_warps : w);
     const size_t masks = (size_t)w * per_warp;
     const size_t need = table + 16 + masks;
     // candidate lists too large to stage whole: stage their first rows (a
@@ -1338,7 +1182,7 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const size_t avail = smem_optin > 16 + masks ? smem_optin - 16 - masks : 0;
     const int part_rows = row ? 0 : (int)(avail / ((size_t)a.cl * 6)) & ~7;
     plan->stage_rows = a.n;
-    const int wave = per_ants * w;  // ants a CTA builds at once
+    const int wave = w;  // ants a CTA builds at once
     if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
         plan->cons_warps = w;
@@ -1356,13 +1200,14 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->smem = (size_t)part_rows * a.cl * 6 + 16 + masks;
     } else {
         plan->staged = 0;
-        plan->cons_warps = 4;
+        plan->cons_warps = plan->wide ? w : 4;
         plan->gen_warps = 0;
-        plan->grid = (a.m + 4 * per_ants - 1) / (4 * per_ants);
-        plan->smem = (size_t)4 * per_warp;
+        const int g = (a.m + plan->cons_warps - 1) / plan->cons_warps;
+        plan->grid = plan->wide && g > num_sms ? num_sms : g;
+        plan->smem = (size_t)plan->cons_warps * per_warp;
     }
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan->staged, plan->tw)
-                     : (plan->pair ? pick_kernel_pair(plan->staged)
+                     : (plan->wide ? pick_kernel_wide(plan->staged)
                                    : pick_kernel(row ? ROW : CAND, plan->staged, plan->tw));
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
@@ -1404,7 +1249,8 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
     }
     const bool var = a.cl == 0 && (a.sel != 0 || a.ct != 0);
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan.staged, plan.tw)
-                     : (plan.pair ? pick_kernel_pair(plan.staged)
+                     : plan.longl ? pick_kernel_long(plan.tw)
+                     : (plan.wide ? pick_kernel_wide(plan.staged)
                                   : pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw));
     k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();

@@ -234,7 +234,8 @@ struct ConstructPlan {
     int staged;     // 0: no staging; 1: the whole table in shared memory; 2: its first stage_rows rows
     int stage_rows;
     int tw;         // tabu words per lane in registers (1, 2, 4; n <= 1024 tw), 0: shared memory
-    int pair;       // 1: two ants per warp (half a warp each; cl <= 16, tw = 0)
+    int wide;       // 1: 32 warps per CTA (MAXT 1024): most rows read from L2
+    int longl;      // 1: 32 < cl <= 64, two candidate slots per lane (k_construct_long)
     int cons_warps; // warps building tours (one ant each) per CTA
     int gen_warps;  // reserved (0)
     int grid;

@@ -12,6 +12,7 @@
 // until the process exits.  Every call shares it: calls whose GPU work overlaps
 // (different streams, no ordering between them) race on it.
 #include <climits>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -138,6 +139,13 @@ extern "C" mmas_status mmas_score_tours_noalloc(const int32_t *d_tours, int32_t 
     }
     if (n < 3 || n > 65535 || pitch < n) {
         set_thread_error("mmas_score_tours_noalloc: need 3 <= n <= 65535 and pitch >= n");
+        return MMAS_EINVAL;
+    }
+    // the kernel reads coordinates as 8-byte pairs and the rest as 4-byte words
+    if ((reinterpret_cast<uintptr_t>(d_xy) & 7u) != 0 || (reinterpret_cast<uintptr_t>(d_tours) & 3u) != 0 ||
+        (reinterpret_cast<uintptr_t>(d_lens) & 3u) != 0 || (reinterpret_cast<uintptr_t>(d_best) & 3u) != 0) {
+        set_thread_error("mmas_score_tours_noalloc: d_xy must be 8-byte aligned and d_tours, d_lens, d_best "
+                         "4-byte aligned");
         return MMAS_EINVAL;
     }
     NoallocScratch *scratch = nullptr;

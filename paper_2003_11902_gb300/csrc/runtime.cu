@@ -132,8 +132,10 @@ mmas_status validate(const mmas_instance *inst, const mmas_params *p)
     if (!(p->rho > 0.0f && p->rho < 1.0f)) return fail(nullptr, MMAS_EINVAL, "rho must be in (0, 1)");
     if (!(p->p_best > 0.0f && p->p_best < 1.0f))
         return fail(nullptr, MMAS_EINVAL, "p_best must be in (0, 1)");
-    if (p->cl < 0 || p->cl > 32 || p->cl >= n)
-        return fail(nullptr, MMAS_EINVAL, "cl must be in [0, min(32, n - 1)]");
+    if (p->cl < 0 || p->cl > 64 || p->cl >= n)
+        return fail(nullptr, MMAS_EINVAL, "cl must be in [0, min(64, n - 1)]");
+    if (p->ls != 0 && p->cl > 32)
+        return fail(nullptr, MMAS_EINVAL, "local search uses the candidate lists as neighbour lists: cl <= 32");
     if (p->deposit != 0 && p->deposit != 1) return fail(nullptr, MMAS_EINVAL, "deposit must be 0 or 1");
     if (p->fallback != 0 && p->fallback != 1)
         return fail(nullptr, MMAS_EINVAL, "fallback must be 0 or 1");
@@ -633,7 +635,6 @@ mmas_status mmas_stats(mmas_handle *h, mmas_stats_t *out)
     out->construct_smem = (int32_t)h->cplan.smem;
     out->row_pitch = h->ld;
     out->fallback_scans = (int64_t)s.fallback_scans;
-    out->construct_ants_per_warp = h->cplan.pair ? 2 : 1;
     return MMAS_OK;
 }
 

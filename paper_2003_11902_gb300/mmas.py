@@ -66,7 +66,7 @@ class mmas_stats_t(C.Structure):
                 ("tau_max", C.c_float), ("construct_grid", C.c_int32),
                 ("construct_block", C.c_int32), ("construct_staged", C.c_int32),
                 ("construct_smem", C.c_int32), ("row_pitch", C.c_int32),
-                ("fallback_scans", C.c_int64), ("construct_ants_per_warp", C.c_int32)]
+                ("fallback_scans", C.c_int64)]
 
 
 class MMASError(RuntimeError):

@@ -49,7 +49,7 @@ def test_default_params(lib):
 
 @pytest.mark.parametrize("field,value,needle", [
     ("rho", 0.0, "rho"), ("rho", 1.0, "rho"), ("p_best", 1.0, "p_best"), ("alpha", -1.0, "alpha"),
-    ("beta", float("nan"), "beta"), ("cl", 33, "cl"), ("cl", -1, "cl"), ("m", -5, "m must"),
+    ("beta", float("nan"), "beta"), ("cl", 65, "cl"), ("cl", -1, "cl"), ("m", -5, "m must"),
     ("deposit", 2, "deposit"), ("fallback", 3, "fallback"), ("ls", 3, "ls"),
     ("selection", 2, "selection"), ("tabu", -1, "tabu"),
 ])
@@ -61,6 +61,13 @@ def test_bad_parameters_are_rejected_before_device_work(lib, field, value, needl
     assert e.value.status == mmas.MMAS_EINVAL
     assert needle in str(e.value)
     assert needle in mmas.mmas_last_error(None)
+
+
+def test_local_search_needs_short_candidate_lists(lib):
+    p = mmas.mmas_default_params()
+    p.cl, p.ls = 40, 1
+    with pytest.raises(mmas.MMASError, match="cl <= 32"):
+        mmas.mmas_create(xy=instances.uniform(50, 1), params=p)
 
 
 def test_bad_instances_are_rejected(lib):

@@ -50,7 +50,7 @@ def _free():
     return torch.cuda.mem_get_info()[0]
 
 
-def _fail_each_allocation(make, limit=80):
+def _fail_each_allocation(make, limit=400):
     """Arm a failure at allocation 0, 1, 2, ... of make() until one succeeds;
     every failed call raises ENOMEM.  Returns how many allocations were hit."""
     for k in range(limit):
