@@ -835,8 +835,9 @@ def _race_from_create(make, seconds, check_every=5):
 def _train_prior(prior, w, count, dev, stream):
     """Train `prior` on the elite tours of `count` generated instances: each
     chunk of 256 runs as one batch of colonies (m = n) for train_iters
-    iterations, then every colony's best tour drives train_steps Adam steps on
-    that colony.  Returns the wall time and the mean first / last loss per chunk."""
+    iterations, then every colony's best tour, improved by the colony's 2-opt
+    (mmas_two_opt_tour, as the races' colonies apply it), drives train_steps
+    Adam steps on that colony.  Returns the wall time and the mean first / last loss per chunk."""
     from paper_2003_11902_gb300 import Batch
     from paper_2003_11902_gb300 import instances as I
 
@@ -851,6 +852,7 @@ def _train_prior(prior, w, count, dev, stream):
         for c in range(len(xys)):
             _, elite = bt.best_tour(c)
             col = bt.colony(c)
+            elite, _ = col.two_opt(elite)  # improved by 2-opt, as the races' colonies improve theirs
             first.append(prior.train(col, elite, steps=1, lr=w["lr"]))
             last.append(prior.train(col, elite, steps=w["train_steps"] - 1, lr=w["lr"]))
             col.close()

@@ -225,6 +225,15 @@ mmas_status mmas_shard_tour(mmas_handle *h, const int64_t *d_key, int32_t *d_tou
  * does nothing and the next synchronising call returns MMAS_ESTATE. */
 mmas_status mmas_update_device(mmas_handle *h, const int32_t *d_tour, const int64_t *d_key);
 
+/* The colony's 2-opt (Sec. 5.7, as ls applies it: the candidate lists as
+ * neighbour lists, don't-look bits, first improvement until no move) applied
+ * to a caller's tour: `tour` (host, n ids, a permutation) is improved in place
+ * and its length written to *len_out (may be NULL).  The colony's state is not
+ * changed.  Needs 1 <= cl <= 32; the first call on a colony created without
+ * local search computes its neighbour distances.  Synchronises.  Errors:
+ * EINVAL (not a permutation, cl, n too large), ESTATE (move cap), ECUDA. */
+mmas_status mmas_two_opt_tour(mmas_handle *h, int32_t *tour, int32_t *len_out);
+
 /* Synchronise and copy the last constructed tours (m x n, row-major) and
  * their lengths (m).  Either pointer may be NULL. */
 mmas_status mmas_get_tours(mmas_handle *h, int32_t *tours, int32_t *lens);

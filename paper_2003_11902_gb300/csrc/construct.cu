@@ -136,8 +136,9 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, co
             const int vq = v0 < n ? v0 : n - 1;
             const uint32_t word = tb.word_of(vq);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
-            w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            // a chunk whose four nodes are visited is not read
+            w4[u] = (c < nch && bits[u] != 0xFu) ? *reinterpret_cast<const float4 *>(row + v0)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -164,6 +165,70 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, co
                     bk = kk;
                     bv = (uint32_t)v;
                 }
+            }
+        }
+    }
+    const uint32_t mx = __reduce_max_sync(FULL, bk);
+    if (mx == 0u) {
+        if (lane == 0) atomicOr(err, ERR_NO_UNVISITED);
+        return cur;
+    }
+    return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+}
+
+// The same selection as scan_row over a row of which at most a few hundred
+// nodes are unvisited, for tabus in shared memory: lane l walks the tabu words
+// l, l + 32, ... and reads the weights of their unvisited nodes only, eight at
+// a time per lane, so a late-tour scan costs a round trip or two and n - t
+// sectors instead of the whole row.  Ties -> lower id (compared explicitly,
+// the nodes are not visited in id order).
+constexpr int SPARSE_SCAN_MAX = 1024;  // unvisited nodes below which the sparse form is used
+
+template <bool GREEDY>
+__device__ __forceinline__ int scan_unvisited(const float *__restrict__ row, int n, const uint32_t *tabu,
+                                              int lane, uint32_t t, uint32_t ant, uint32_t it,
+                                              uint32_t k0, uint32_t k1, uint32_t *err, int cur)
+{
+    constexpr int U = 8;
+    const int nw = (n + 31) >> 5;
+    const uint32_t tail = (n & 31) ? (1u << (n & 31)) - 1u : 0xFFFFFFFFu;
+    uint32_t bk = 0u, bv = 0xFFFFFFFFu;
+    int q = lane;
+    uint32_t pend = q < nw ? ~tabu[q] & (q == nw - 1 ? tail : 0xFFFFFFFFu) : 0u;
+    for (;;) {
+        int vs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            while (pend == 0u && q < nw) {
+                q += 32;
+                pend = q < nw ? ~tabu[q] & (q == nw - 1 ? tail : 0xFFFFFFFFu) : 0u;
+            }
+            if (pend != 0u) {
+                vs[u] = (q << 5) + __ffs(pend) - 1;
+                pend &= pend - 1u;
+            } else {
+                vs[u] = -1;
+            }
+        }
+        if (!__any_sync(FULL, vs[0] >= 0)) break;
+        float x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = vs[u] >= 0 ? row[vs[u]] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (vs[u] < 0) continue;
+            const uint32_t v = (uint32_t)vs[u];
+            uint32_t kk;
+            if constexpr (GREEDY) {
+                kk = ord_key(x[u]);
+            } else {
+                uint4 r = make_uint4(0x80000000u | (v >> 2), t, ant, it);
+                philox_rounds<0, 10>(r, k0, k1);
+                kk = ord_key(__fmul_rn(log2f(unit_open(pick_word(r, (int)(v & 3u)))), __frcp_rn(x[u])));
+            }
+            if (kk > bk || (kk == bk && v < bv)) {
+                bk = kk;
+                bv = v;
             }
         }
     }
@@ -238,13 +303,16 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
                                           const uint2 *xl, const float *xb, const uint2 *xx,
                                           const int32_t *xn, int xe)
 {
+    const bool sparse = TW == 0 && n - (int)t <= SPARSE_SCAN_MAX;  // few nodes left: read only those
     if (mode == 0) {
         if (xe > 0) {
             const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane);
             if (r >= 0) return r;
         }
+        if (sparse) return scan_unvisited<true>(row, n, tb.w, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
         return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
     }
+    if (sparse) return scan_unvisited<false>(row, n, tb.w, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
     return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
 }
 
@@ -1105,11 +1173,8 @@ KernelFn pick_kernel(int mode, int staged, int tw)
     return mode == CAND ? cand[staged][ti] : rowk[staged ? 1 : 0][ti];
 }
 
-// the 32-warp form, tabus in shared memory: staged rows (2) or none (0)
-KernelFn pick_kernel_wide(int staged)
-{
-    return staged == 2 ? k_construct<CAND, 2, 0, 1024> : k_construct<CAND, 0, 0, 1024>;
-}
+// the 32-warp form, tabus in shared memory, rows read through L1 and L2
+KernelFn pick_kernel_wide(int) { return k_construct<CAND, 0, 0, 1024>; }
 
 KernelFn pick_kernel_long(int tw)
 {
@@ -1156,8 +1221,8 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
     }
     // most rows of the candidate table unstageable (under a quarter of it fits
-    // beside the tabus of 12 warps): 32 warps per CTA (MAXT = 1024), which
-    // stage the rows that still fit beside their tabus
+    // beside the tabus of 12 warps): 32 warps per CTA (MAXT = 1024), the rows
+    // read through L1 and L2
     plan->wide = 0;
     if (!row && !var && plan->tw == 0) {
         const size_t tabus12 = (size_t)12 * nw * sizeof(uint32_t);
@@ -1183,7 +1248,17 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     const int part_rows = row ? 0 : (int)(avail / ((size_t)a.cl * 6)) & ~7;
     plan->stage_rows = a.n;
     const int wave = w;  // ants a CTA builds at once
-    if (need <= smem_optin && table < (1u << 30)) {
+    if (plan->wide) {
+        // no staging: shared memory holds only the tabus, which leaves L1 room
+        // to cache the candidate rows (measured faster than staging the few
+        // rows that fit: 84 -> 69 ms at n = 18,500)
+        plan->staged = 0;
+        plan->cons_warps = w;
+        plan->gen_warps = 0;
+        const int g = (a.m + w - 1) / w;
+        plan->grid = g < num_sms ? g : num_sms;
+        plan->smem = (size_t)w * per_warp;
+    } else if (need <= smem_optin && table < (1u << 30)) {
         plan->staged = 1;
         plan->cons_warps = w;
         plan->gen_warps = 0;
@@ -1200,11 +1275,10 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->smem = (size_t)part_rows * a.cl * 6 + 16 + masks;
     } else {
         plan->staged = 0;
-        plan->cons_warps = plan->wide ? w : 4;
+        plan->cons_warps = 4;
         plan->gen_warps = 0;
-        const int g = (a.m + plan->cons_warps - 1) / plan->cons_warps;
-        plan->grid = plan->wide && g > num_sms ? num_sms : g;
-        plan->smem = (size_t)plan->cons_warps * per_warp;
+        plan->grid = (a.m + 3) / 4;
+        plan->smem = (size_t)4 * per_warp;
     }
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan->staged, plan->tw)
                      : (plan->wide ? pick_kernel_wide(plan->staged)

@@ -516,6 +516,40 @@ mmas_status mmas_construct(mmas_handle *h)
     return MMAS_OK;
 }
 
+mmas_status mmas_two_opt_tour(mmas_handle *h, int32_t *tour, int32_t *len_out)
+{
+    if (check_handle(h)) return MMAS_EINVAL;
+    if (!tour) return fail(h, MMAS_EINVAL, "tour must be non-NULL");
+    if (h->cl < 1 || h->cl > 32) return fail(h, MMAS_EINVAL, "2-opt uses the candidate lists: 1 <= cl <= 32");
+    if (!two_opt_fits(h->n, h->cl, false, (size_t)h->smem_optin))
+        return fail(h, MMAS_EINVAL, "2-opt needs about 12.1n bytes of shared memory per CTA: n is too large");
+    std::vector<char> seen((size_t)h->n, 0);
+    for (int i = 0; i < h->n; ++i) {
+        const int v = tour[i];
+        if (v < 0 || v >= h->n || seen[v]) return fail(h, MMAS_EINVAL, "tour must be a permutation of 0..n-1");
+        seen[v] = 1;
+    }
+    DeviceGuard g(h->device);
+    if (!h->nnd) {  // neighbour distances, once, as a colony with local search has them
+        CK(h, dalloc(&h->nnd, (size_t)h->n * h->cl * sizeof(int32_t), h->stream));
+        CK(h, launch_neighbour_dist(h->targs, h->nnd, h->stream));
+        h->targs.nnd = h->nnd;
+    }
+    CK(h, cudaMemcpyAsync(h->ext_tour, tour, (size_t)h->n * 4, cudaMemcpyHostToDevice, h->stream));
+    TwoOptArgs ta = h->targs;
+    ta.m = 1;
+    ta.tours = h->ext_tour;
+    ta.lens = h->ext_len;
+    CK(h, launch_two_opt(ta, false, h->num_sms, (int)h->smem_optin, h->stream));
+    int32_t len = 0;
+    CK(h, cudaMemcpyAsync(tour, h->ext_tour, (size_t)h->n * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(&len, h->ext_len, sizeof(len), cudaMemcpyDeviceToHost, h->stream));
+    mmas_status st = sync_and_check(h);
+    if (st != MMAS_OK) return st;
+    if (len_out) *len_out = len;
+    return MMAS_OK;
+}
+
 mmas_status mmas_update(mmas_handle *h, const int32_t *tour, int32_t len)
 {
     if (check_handle(h)) return MMAS_EINVAL;

@@ -29,7 +29,7 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
            "mmas_debug_fail_allocation", "mmas_debug_expire_stage_waits",
-           "mmas_shard_best_key", "mmas_shard_tour", "mmas_update_device",
+           "mmas_shard_best_key", "mmas_shard_tour", "mmas_update_device", "mmas_two_opt_tour",
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
            "mmas_probe_l2_bandwidth",
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
             "mmas_shard_best_key": (C.c_int, [H, C.c_void_p]),
             "mmas_shard_tour": (C.c_int, [H, C.c_void_p, C.c_void_p]),
             "mmas_update_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+            "mmas_two_opt_tour": (C.c_int, [H, P(i32), P(i32)]),
             "mmas_debug_expire_stage_waits": (C.c_int, [i32, i32]),
             "mmas_synchronize": (C.c_int, [H]),
             "mmas_enable_phase_timing": (C.c_int, [H, i32]),
@@ -406,6 +407,13 @@ class Colony:
 
     def stats(self) -> dict:
         return mmas_stats(self._h)
+
+    def two_opt(self, tour):
+        """The colony's 2-opt applied to a copy of `tour`: (improved tour, length)."""
+        t = np.array(tour, dtype=np.int32, copy=True, order="C")
+        n = C.c_int32()
+        _check(self._h, load().mmas_two_opt_tour(self._h, _i32p(t), C.byref(n)))
+        return t, n.value
 
     def shard_best_key(self, key):
         """Enqueue: the device int64 `key` (a tensor or an address) = (length
