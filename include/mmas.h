@@ -276,6 +276,14 @@ void mmas_debug_fail_allocation(int32_t after);
  * restores normal waits.  Errors: EINVAL (bad device), ECUDA. */
 mmas_status mmas_debug_expire_stage_waits(int32_t device, int32_t on);
 
+/* Testing aid for the 2-opt search's guard (not part of the method): every
+ * improving move shortens the tour, so a search ends by itself; a cap of 64 n
+ * moves per tour only guards against a defect.  cap > 0 replaces it on
+ * `device` (a search that reaches it stops, keeps the moves made, and the next
+ * synchronising call returns MMAS_ESTATE); cap <= 0 restores 64 n.
+ * Errors: EINVAL (bad device), ECUDA. */
+mmas_status mmas_debug_two_opt_move_cap(int32_t device, int64_t cap);
+
 /* Block until all work enqueued by the handle has finished; report device-side
  * errors (ETIMEOUT, ESTATE) raised since the last check. */
 mmas_status mmas_synchronize(mmas_handle *h);
@@ -329,6 +337,15 @@ mmas_status mmas_probe_l2_bandwidth(int32_t device, int64_t bytes, double *gbs);
 mmas_status mmas_gemm_bf16(const void *d_a, int32_t lda, const void *d_b, int32_t ldb,
                            const float *d_bias, float *d_out, int32_t ldd, int32_t m, int32_t n,
                            int32_t k, int32_t relu, void *stream);
+
+/* The same product accumulated, for long K (the weight gradients of the
+ * learned prior, K = n):  out[m][j] += sum_k A[m][k] * B[j][k].  The K blocks
+ * (64 wide) are split over CTAs, up to one per SM, each adding its partial
+ * 128 x n tile into d_out with fp32 atomic adds, so the order of the additions
+ * (and the last bits of the result) may vary between calls.  Arguments and
+ * errors as for mmas_gemm_bf16 (no bias or activation). */
+mmas_status mmas_gemm_bf16_acc(const void *d_a, int32_t lda, const void *d_b, int32_t ldb, float *d_out,
+                               int32_t ldd, int32_t m, int32_t n, int32_t k, void *stream);
 
 /* ---- learned edge prior ---------------------------------------------------
  *

@@ -12,8 +12,11 @@
 // canonical K-major 128-byte-swizzled layout (rows of 128 bytes, 8-row atoms of
 // 1 KB, the 16-byte chunk c of row r stored at chunk c ^ (r mod 8)); one thread
 // issues four MMAs (K = 16 each, the descriptor start advanced by 32 bytes)
-// and commits them to an mbarrier that every thread waits on (bounded) before
-// the tiles are overwritten.  The accumulator lives in TMEM (N columns); the
+// and commits them to the stage's mbarrier.  Two stages: block i + 1 is copied
+// while the MMAs of block i run, and a stage is rewritten only after its MMAs
+// completed (bounded waits).  Split-K (launch_gemm_bf16_splitk): CTAs along
+// grid.y take disjoint ranges of K blocks and atomically add their fp32 tiles
+// into a zeroed output, for the long-K products (K = n) of the weight gradients.  The accumulator lives in TMEM (N columns); the
 // epilogue reads it with tcgen05.ld (warp w owns rows 32w .. 32w+31), applies
 // bias, residual and ReLU, and stores D.
 #include <cuda_bf16.h>
@@ -39,6 +42,8 @@ struct GemmArgs {
     __nv_bfloat16 *d16;     // bf16 output or nullptr
     int m, n, k, lda, ldb, ldd, ldr, relu;
     uint32_t *err;          // set on an MMA-completion timeout
+    int kb_per_split;       // K blocks per CTA along grid.y (split-K)
+    int accumulate;         // 1: atomically add the fp32 tile into d32 (split-K), no epilogue ops
 };
 
 // Canonical UMMA shared-memory descriptor (tcgen05): start address >> 4,
@@ -129,12 +134,17 @@ __device__ __forceinline__ void load_tile(uint8_t *tile, const __nv_bfloat16 *sr
 template <int N>
 __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g)
 {
-    __shared__ __align__(1024) uint8_t s_a[TM * 128];
-    __shared__ __align__(1024) uint8_t s_b[N * 128];
-    __shared__ __align__(8) uint64_t s_bar;
+    // two stages: the tiles of K block i + 1 are written while the MMAs of
+    // block i run; a stage is rewritten only after the MMAs that read it
+    // completed (its own mbarrier)
+    extern __shared__ uint8_t dsmem[];  // gemm_smem_bytes(N): two stages, 1024-byte aligned below
+    __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ uint32_t s_tmem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TM;
+    // the swizzled tiles start on 1024-byte boundaries (the descriptors' atoms)
+    uint8_t *const tiles = dsmem + ((1024u - (smem_u32(dsmem) & 1023u)) & 1023u);
+    // stage st: A tile at tiles + st * TM * 128, B tile at tiles + 2 TM 128 + st * N * 128
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -143,39 +153,54 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
     constexpr uint32_t idesc = instr_desc(TM, N);
 
-    bool ok = true;
+    // this CTA's K blocks: [kb0, kb1)
     const int kblocks = (g.k + TK - 1) / TK;
-    for (int kb = 0; kb < kblocks; ++kb) {
-        load_tile(s_a, g.a, g.lda, m0, TM, g.m, kb * TK, g.k);
-        load_tile(s_b, g.b, g.ldb, 0, N, g.n, kb * TK, g.k);
+    const int kb0 = blockIdx.y * g.kb_per_split;
+    const int kb1 = min(kblocks, kb0 + g.kb_per_split);
+    const int nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+        const int st = i & 1, kb = kb0 + i;
+        if (i >= 2) {  // the MMAs of block i - 2 read this stage
+            const bool done = mbar_wait_bounded(&s_bar[st], (uint32_t)(((i - 2) >> 1) & 1), MMA_LIMIT_NS);
+            if (!__syncthreads_and(done)) {
+                ok = false;
+                break;
+            }
+        }
+        uint8_t *const sa = tiles + st * (TM * 128);
+        uint8_t *const sb = tiles + 2 * (TM * 128) + st * (N * 128);
+        load_tile(sa, g.a, g.lda, m0, TM, g.m, kb * TK, g.k);
+        load_tile(sb, g.b, g.ldb, 0, N, g.n, kb * TK, g.k);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async reads
         __syncthreads();
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t ad = smem_desc(smem_u32(s_a)), bd = smem_desc(smem_u32(s_b));
+            const uint64_t ad = smem_desc(smem_u32(sa)), bd = smem_desc(smem_u32(sb));
 #pragma unroll
             for (int ks = 0; ks < TK / 16; ++ks)  // 16 bf16 = 32 bytes = 2 descriptor units
-                mma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-            mma_commit(&s_bar);
+                mma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(&s_bar[st]);
         }
-        // the MMAs have read the tiles (and, after the last block, written D);
-        // the decision to stop on a timeout is taken by the whole CTA
-        const bool done = mbar_wait_bounded(&s_bar, (uint32_t)(kb & 1), MMA_LIMIT_NS);
-        if (!__syncthreads_and(done)) {
-            ok = false;
-            break;
-        }
+    }
+    if (ok && nkb > 0) {  // the last commit covers every earlier MMA of this thread
+        const int last = nkb - 1;
+        const bool done = mbar_wait_bounded(&s_bar[last & 1], (uint32_t)((last >> 1) & 1), MMA_LIMIT_NS);
+        ok = __syncthreads_and(done) != 0;
     }
     if (!ok) {
         if (threadIdx.x == 0) atomicOr(g.err, ERR_STAGE_TIMEOUT);
-    } else if (kblocks > 0) {
+    } else if (nkb > 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m0 + warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
@@ -189,6 +214,10 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g)
                     const int col = c0 + i;
                     if (col >= g.n) break;
                     float x = v[i];
+                    if (g.accumulate) {
+                        atomicAdd(g.d32 + (size_t)row * g.ldd + col, x);
+                        continue;
+                    }
                     if (g.bias) x += g.bias[col];
                     if (g.relu) x = fmaxf(x, 0.0f);
                     if (g.resid) x += g.resid[(size_t)row * g.ldr + col];
@@ -207,6 +236,24 @@ __global__ void __launch_bounds__(128, 1) k_gemm_bf16(const GemmArgs g)
     }
 }
 
+// Dynamic shared memory of k_gemm_bf16<N>: two stages of the A and B tiles
+// plus room to align them to 1024 bytes.
+constexpr int gemm_smem_bytes(int n) { return 2 * (TM * 128 + n * 128) + 1024; }
+
+template <int N>
+cudaError_t launch_gemm_tile(const GemmArgs &g, dim3 grid, cudaStream_t s)
+{
+    static bool attr = false;  // per process: the attribute applies to the kernel
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   gemm_smem_bytes(N));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_gemm_bf16<N><<<grid, 128, gemm_smem_bytes(N), s>>>(g);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_gemm_bf16(const __nv_bfloat16 *a, int lda, const __nv_bfloat16 *b, int ldb,
@@ -214,14 +261,29 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *a, int lda, const __nv_bfloat1
                              __nv_bfloat16 *d16, int ldd, int m, int n, int k, int relu,
                              uint32_t *err, cudaStream_t s)
 {
-    GemmArgs g{a, b, bias, resid, d32, d16, m, n, k, lda, ldb, ldd, ldr, relu, err};
+    const int kblocks = (k + TK - 1) / TK;
+    GemmArgs g{a, b, bias, resid, d32, d16, m, n, k, lda, ldb, ldd, ldr, relu, err, kblocks > 0 ? kblocks : 1, 0};
     const int grid = (m + TM - 1) / TM;
     if (grid == 0) return cudaSuccess;
-    if (n <= 64)
-        k_gemm_bf16<64><<<grid, 128, 0, s>>>(g);
-    else
-        k_gemm_bf16<128><<<grid, 128, 0, s>>>(g);
-    return cudaGetLastError();
+    return n <= 64 ? launch_gemm_tile<64>(g, dim3(grid), s) : launch_gemm_tile<128>(g, dim3(grid), s);
+}
+
+cudaError_t launch_gemm_bf16_splitk(const __nv_bfloat16 *a, int lda, const __nv_bfloat16 *b, int ldb,
+                                    float *d32, int ldd, int m, int n, int k, int max_ctas, uint32_t *err,
+                                    cudaStream_t s)
+{
+    const int kblocks = (k + TK - 1) / TK;
+    const int gx = (m + TM - 1) / TM;
+    if (gx == 0 || kblocks == 0) return cudaSuccess;
+    // split K so that the CTAs cover up to max_ctas SMs, at least two K blocks each
+    int splits = max_ctas / gx;
+    splits = splits < 1 ? 1 : splits;
+    if (splits > (kblocks + 1) / 2) splits = (kblocks + 1) / 2;
+    const int per = (kblocks + splits - 1) / splits;
+    splits = (kblocks + per - 1) / per;
+    GemmArgs g{a, b, nullptr, nullptr, d32, nullptr, m, n, k, lda, ldb, ldd, 0, 0, err, per, 1};
+    const dim3 grid(gx, splits);
+    return n <= 64 ? launch_gemm_tile<64>(g, grid, s) : launch_gemm_tile<128>(g, grid, s);
 }
 
 }  // namespace mmas
@@ -255,6 +317,38 @@ extern "C" mmas_status mmas_gemm_bf16(const void *d_a, int32_t lda, const void *
     }
     if (h_err) {
         set_thread_error("mmas_gemm_bf16: an MMA did not complete in time");
+        return MMAS_ETIMEOUT;
+    }
+    return MMAS_OK;
+}
+
+extern "C" mmas_status mmas_gemm_bf16_acc(const void *d_a, int32_t lda, const void *d_b, int32_t ldb, float *d_out,
+                                          int32_t ldd, int32_t m, int32_t n, int32_t k, void *stream)
+{
+    if (!d_a || !d_b || !d_out || m < 0 || k < 0 || n < 1 || n > 128 || lda < k || ldb < k || ldd < n) {
+        set_thread_error("mmas_gemm_bf16_acc: need non-NULL A, B, out; 1 <= n <= 128; lda, ldb >= k; ldd >= n");
+        return MMAS_EINVAL;
+    }
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t *err = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMallocAsync(&err, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess)
+        e = launch_gemm_bf16_splitk(static_cast<const __nv_bfloat16 *>(d_a), lda,
+                                    static_cast<const __nv_bfloat16 *>(d_b), ldb, d_out, ldd, m, n, k, sms, err, s);
+    uint32_t h_err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (err) cudaFreeAsync(err, s);
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("mmas_gemm_bf16_acc: ") + cudaGetErrorString(e));
+        return MMAS_ECUDA;
+    }
+    if (h_err) {
+        set_thread_error("mmas_gemm_bf16_acc: an MMA did not complete in time");
         return MMAS_ETIMEOUT;
     }
     return MMAS_OK;

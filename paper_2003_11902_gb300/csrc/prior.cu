@@ -35,6 +35,9 @@ cudaError_t launch_gemm_bf16(const __nv_bfloat16 *a, int lda, const __nv_bfloat1
                              const float *bias, const float *resid, int ldr, float *d32,
                              __nv_bfloat16 *d16, int ldd, int m, int n, int k, int relu,
                              uint32_t *err, cudaStream_t s);
+cudaError_t launch_gemm_bf16_splitk(const __nv_bfloat16 *a, int lda, const __nv_bfloat16 *b, int ldb,
+                                    float *d32, int ldd, int m, int n, int k, int max_ctas, uint32_t *err,
+                                    cudaStream_t s);
 }
 
 namespace {
@@ -304,6 +307,7 @@ struct mmas_prior {
     float *params = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     bf16 *w0 = nullptr, *wl = nullptr, *wlt = nullptr, *wq = nullptr, *wqt = nullptr;
     int adam_t = 0;
+    int num_sms = 0;  // of the prior's device, looked up at the first split-K product
     bool packed = false;
     // workspace for an n-node instance
     int cap = 0;
@@ -414,6 +418,16 @@ mmas_status gemm(mmas_prior *p, const bf16 *a, int lda, const bf16 *b, int ldb, 
                  cudaStream_t s)
 {
     PCK(p, launch_gemm_bf16(a, lda, b, ldb, bias, resid, ldr, d32, d16, ldd, m, nn, k, relu, p->err, s));
+    return MMAS_OK;
+}
+
+// A weight gradient d32 += A B^T with K = n: K is split over CTAs that add
+// their partial products into d32, which the training step zeroed.
+mmas_status gemm_wgrad(mmas_prior *p, const bf16 *a, int lda, const bf16 *b, int ldb, float *d32, int ldd, int m,
+                       int nn, int k, cudaStream_t s)
+{
+    if (!p->num_sms) PCK(p, cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    PCK(p, launch_gemm_bf16_splitk(a, lda, b, ldb, d32, ldd, m, nn, k, p->num_sms, p->err, s));
     return MMAS_OK;
 }
 
@@ -604,8 +618,7 @@ mmas_status mmas_prior_train(mmas_prior *p, mmas_handle *h, const int32_t *tour,
         transpose(p->hb[3], n, H, p->hbT);
         PCK(p, cudaGetLastError());
         // dWq = dq^T h3 ;  dh3 += dq Wq
-        if ((st = gemm(p, p->dqT, n, p->hbT, n, nullptr, nullptr, 0, p->grad + O_WQ, nullptr, H, H, H, n, 0, s)))
-            return st;
+        if ((st = gemm_wgrad(p, p->dqT, n, p->hbT, n, p->grad + O_WQ, H, H, H, n, s))) return st;
         if ((st = gemm(p, p->dqb, H, p->wqt, H, nullptr, p->dh, H, p->dh, nullptr, H, n, H, H, 0, s))) return st;
         for (int l = 3; l >= 1; --l) {
             // da = dh on the active units; db_l; dW_l = da^T z_l; dz = da W_l
@@ -613,9 +626,7 @@ mmas_status mmas_prior_train(mmas_prior *p, mmas_handle *h, const int32_t *tour,
                                                                        p->daT, p->grad + o_bl(l));
             transpose(p->z[l], n, 2 * H, p->zT);
             PCK(p, cudaGetLastError());
-            if ((st = gemm(p, p->daT, n, p->zT, n, nullptr, nullptr, 0, p->grad + o_wl(l), nullptr, 2 * H, H, 2 * H,
-                           n, 0, s)))
-                return st;
+            if ((st = gemm_wgrad(p, p->daT, n, p->zT, n, p->grad + o_wl(l), 2 * H, H, 2 * H, n, s))) return st;
             if ((st = gemm(p, p->dab, H, p->wlt + (size_t)(l - 1) * H * 2 * H, H, nullptr, nullptr, 0, p->dz, nullptr,
                            2 * H, n, 2 * H, H, 0, s)))
                 return st;
@@ -630,8 +641,7 @@ mmas_status mmas_prior_train(mmas_prior *p, mmas_handle *h, const int32_t *tour,
                                                                    p->grad + O_B0);
         transpose(p->F, n, FIN, p->FT);
         PCK(p, cudaGetLastError());
-        if ((st = gemm(p, p->daT, n, p->FT, n, nullptr, nullptr, 0, p->grad + O_W0, nullptr, FIN, H, FIN, n, 0, s)))
-            return st;
+        if ((st = gemm_wgrad(p, p->daT, n, p->FT, n, p->grad + O_W0, FIN, H, FIN, n, s))) return st;
         // Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
         p->adam_t += 1;
         // bias corrections 1 - beta^t of the single-precision betas, in double

@@ -401,6 +401,17 @@ extern "C" {
 
 void mmas_debug_fail_allocation(int32_t after) { g_fail_after.store(after < 0 ? -1 : after); }
 
+mmas_status mmas_debug_two_opt_move_cap(int32_t device, int64_t cap)
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, MMAS_EINVAL, "device ordinal out of range");
+    DeviceGuard g(device);
+    const cudaError_t e = set_two_opt_move_cap(cap);
+    if (e != cudaSuccess) return fail(nullptr, MMAS_ECUDA, std::string("set_two_opt_move_cap: ") + cudaGetErrorString(e));
+    return MMAS_OK;
+}
+
 mmas_status mmas_debug_expire_stage_waits(int32_t device, int32_t on)
 {
     int ndev = 0;

@@ -45,6 +45,10 @@ namespace mmas {
 
 namespace {
 
+// Testing aid (mmas_debug_two_opt_move_cap): when positive, replaces the move
+// cap of 64 n, so a test can make a search hit it.
+__device__ long long g_two_opt_cap;
+
 
 // Shared-memory layout (byte offsets), identical on host and device.
 struct Layout {
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
         __syncthreads();
         // every move shortens the tour by >= 1, so the search ends; the cap
         // (far above the moves a tour needs) only guards against a defect
-        const long long cap = 64LL * n;
+        const long long cap = g_two_opt_cap > 0 ? g_two_opt_cap : 64LL * n;
         long long total = 0;
         bool capped = false;
         uint32_t round = 0;  // selects the key slot
@@ -459,6 +463,12 @@ cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_
     else
         k_neighbour_dist<false><<<256, 256, 0, s>>>(a, nnd);
     return cudaGetLastError();
+}
+
+cudaError_t set_two_opt_move_cap(long long cap)
+{
+    const long long v = cap > 0 ? cap : 0;
+    return cudaMemcpyToSymbol(g_two_opt_cap, &v, sizeof(v));
 }
 
 cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, int smem_optin,

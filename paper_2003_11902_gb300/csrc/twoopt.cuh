@@ -27,5 +27,8 @@ bool two_opt_fits(int n, int k, bool staged, size_t smem_optin);
 cudaError_t launch_two_opt(const TwoOptArgs &a, bool iteration_best, int num_sms, int smem_optin,
                            cudaStream_t s);
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s);
+// Testing aid: the move cap of the 2-opt search on the current device
+// (cap <= 0: the default 64 n).
+cudaError_t set_two_opt_move_cap(long long cap);
 
 }  // namespace mmas

@@ -28,10 +28,10 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_destroy", "mmas_last_error", "mmas_construct", "mmas_update",
            "mmas_get_tours", "mmas_get_pheromone", "mmas_set_pheromone", "mmas_get_setup",
            "mmas_set_iteration", "mmas_stats", "mmas_synchronize", "mmas_enable_phase_timing",
-           "mmas_debug_fail_allocation", "mmas_debug_expire_stage_waits",
+           "mmas_debug_fail_allocation", "mmas_debug_expire_stage_waits", "mmas_debug_two_opt_move_cap",
            "mmas_shard_best_key", "mmas_shard_tour", "mmas_update_device", "mmas_two_opt_tour",
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
-           "mmas_probe_l2_bandwidth",
+           "mmas_probe_l2_bandwidth", "mmas_gemm_bf16_acc",
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
            "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
            "mmas_prior_destroy", "mmas_prior_last_error", "mmas_prior_apply_weighted",
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
             "mmas_update_device": (C.c_int, [H, C.c_void_p, C.c_void_p]),
             "mmas_two_opt_tour": (C.c_int, [H, P(i32), P(i32)]),
             "mmas_debug_expire_stage_waits": (C.c_int, [i32, i32]),
+            "mmas_debug_two_opt_move_cap": (C.c_int, [i32, i64]),
             "mmas_synchronize": (C.c_int, [H]),
             "mmas_enable_phase_timing": (C.c_int, [H, i32]),
             "mmas_phase_times": (C.c_int, [H, P(f32), P(f32), P(f32)]),
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH):
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
             "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
             "mmas_probe_l2_bandwidth": (C.c_int, [i32, i64, P(C.c_double)]),
+            "mmas_gemm_bf16_acc": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, i32, i32, i32, i32,
+                                            C.c_void_p]),
             "mmas_gemm_bf16": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, C.c_void_p,
                                         i32, i32, i32, i32, i32, C.c_void_p]),
             "mmas_prior_create": (C.c_int, [P(f32), i32, P(H)]),
@@ -296,6 +299,12 @@ def mmas_debug_expire_stage_waits(device: int, on: bool):
     _check(None, load().mmas_debug_expire_stage_waits(int(device), int(bool(on))))
 
 
+def mmas_debug_two_opt_move_cap(device: int, cap: int):
+    """Replace the 2-opt search's move cap on `device` (cap <= 0: the default);
+    a testing aid, see include/mmas.h."""
+    _check(None, load().mmas_debug_two_opt_move_cap(int(device), int(cap)))
+
+
 def mmas_synchronize(h):
     _check(h, load().mmas_synchronize(h))
 
@@ -464,6 +473,15 @@ def mmas_gemm_bf16(d_a: int, lda: int, d_b: int, ldb: int, d_bias, d_out: int, l
         stream = _torch_stream()
     _check(None, load().mmas_gemm_bf16(d_a, lda, d_b, ldb, d_bias, d_out, ldd, m, n, k,
                                        int(relu), stream))
+
+
+def mmas_gemm_bf16_acc(d_a: int, lda: int, d_b: int, ldb: int, d_out: int, ldd: int, m: int, n: int, k: int,
+                       stream=None):
+    """out += A B^T on the tensor cores with K split over CTAs (device
+    addresses); see include/mmas.h."""
+    if stream is None:
+        stream = _torch_stream()
+    _check(None, load().mmas_gemm_bf16_acc(d_a, lda, d_b, ldb, d_out, ldd, m, n, k, stream))
 
 
 # ------------------------------------------------------------------- learned prior

@@ -4,7 +4,9 @@ that is made to run out -- never by faulting the GPU:
   - a simulated device out-of-memory at every allocation of mmas_create,
     mmas_batch_create and the learned prior: ENOMEM, nothing left allocated;
   - the construction's staging wait made to run out: ETIMEOUT at the next
-    synchronising call, and the device stays usable."""
+    synchronising call, and the device stays usable;
+  - the 2-opt search's move cap made small enough to be hit: ESTATE, the
+    tours still permutations."""
 import numpy as np
 import pytest
 
@@ -22,6 +24,7 @@ def built():
     yield
     mmas.mmas_debug_fail_allocation(-1)
     mmas.mmas_debug_expire_stage_waits(0, False)
+    mmas.mmas_debug_two_opt_move_cap(0, 0)
 
 
 def test_tour_length_overflow_is_refused():
@@ -122,4 +125,22 @@ def test_staging_wait_that_runs_out_reports_a_timeout():
     g.iterate(1)
     o.iterate(1)
     assert np.array_equal(g.tours()[0], o.tours()[0])
+    g.close()
+
+
+def test_two_opt_move_cap_reports_a_state_error():
+    xy = I.uniform(400, 21)
+    g = Colony(xy=xy, m=32, cl=16, seed=4, ls=2)
+    mmas.mmas_debug_two_opt_move_cap(0, 3)
+    try:
+        g.iterate(1)
+        with pytest.raises(MMASError, match="move cap") as e:
+            g.synchronize()
+        assert e.value.status == mmas.MMAS_ESTATE
+    finally:
+        mmas.mmas_debug_two_opt_move_cap(0, 0)
+    tours, _ = g.tours()
+    assert all(sorted(t) == list(range(400)) for t in tours)  # stopped searches keep whole tours
+    g.iterate(1)
+    g.synchronize()  # the default cap: no error
     g.close()

@@ -56,3 +56,26 @@ def test_gemm_rejects_bad_shapes():
     o = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(mmas.MMASError, match="n <= 128"):
         mmas.mmas_gemm_bf16(t.data_ptr(), 4, t.data_ptr(), 4, None, o.data_ptr(), 4, 4, 129, 4)
+
+
+@pytest.mark.parametrize("m,n,k", [
+    (64, 64, 2000),     # a weight gradient's shape: 64 x 64, K = n (32 K blocks over 16 CTAs)
+    (128, 128, 3000),   # 128 x 128, K = 3000 (ragged last block)
+    (200, 64, 130),     # two row tiles, three K blocks
+    (8, 64, 18500),     # the input layer's weight gradient at n = 18,500
+])
+def test_split_k_accumulating_gemm_matches_exact_product(m, n, k):
+    # out += A B^T with K split over CTAs (fp32 atomic adds of the partial tiles)
+    rng = np.random.default_rng(m + n + k)
+    a = rng.standard_normal((m, k)).astype(np.float32)
+    b = rng.standard_normal((n, k)).astype(np.float32)
+    ta, tb = _bf16(a).cuda(), _bf16(b).cuda()
+    out0 = rng.standard_normal((m, n)).astype(np.float32)
+    out = torch.from_numpy(out0).cuda()
+    mmas.mmas_gemm_bf16_acc(ta.data_ptr(), k, tb.data_ptr(), k, out.data_ptr(), n, m, n, k)
+    want = out0.astype(np.float64) + ta.float().cpu().numpy().astype(np.float64) @ \
+        tb.float().cpu().numpy().astype(np.float64).T
+    got = out.cpu().numpy()
+    scale = np.abs(ta.float().cpu().numpy()) @ np.abs(tb.float().cpu().numpy()).T + np.abs(out0)
+    # fp32 accumulation inside each split and the atomic adds of the splits
+    assert np.all(np.abs(got - want) <= 1e-6 + (k + 64) * 2.0 ** -23 * (scale + 1e-30))
