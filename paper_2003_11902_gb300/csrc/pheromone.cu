@@ -357,11 +357,19 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
     float4 *trow = reinterpret_cast<float4 *>(a.tau + (size_t)i * a.ld);
     const float4 *erow = reinterpret_cast<const float4 *>(a.eb + (size_t)i * a.ld);
     float4 *wrow = reinterpret_cast<float4 *>(a.wmat + (size_t)i * a.ld);
+    // the next round's loads are issued before this round's arithmetic, so a
+    // warp keeps two rounds of the row in flight
+    float4 t4n = lane < nq ? trow[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 e4n = lane < nq ? __ldg(erow + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int q0 = 0; q0 < nq; q0 += 32) {  // every lane takes each round
         const int q = q0 + lane;
         const bool inq = q < nq;
-        const float4 t4 = inq ? trow[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 e4 = inq ? __ldg(erow + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 t4 = t4n;
+        const float4 e4 = e4n;
+        if (q + 32 < nq) {
+            t4n = trow[q + 32];
+            e4n = __ldg(erow + q + 32);
+        }
         float tv[4] = {t4.x, t4.y, t4.z, t4.w};
         const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
         float wv[4];
