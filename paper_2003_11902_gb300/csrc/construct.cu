@@ -117,7 +117,9 @@ __device__ __forceinline__ float pick_f(const float4 &r, int e)
 // fallback on choice_info); otherwise the reservoir key log2(r) * inv-weight,
 // r from the whole-row stream, with `row` holding the reciprocal weights (RECIP)
 // or the weights.  Eight chunk-columns (1024 nodes) are loaded before use, so
-// rows of up to 1024 nodes cost one memory round trip.
+// rows of up to 1024 nodes cost one memory round trip.  The loads are
+// streaming (evict-first): a scanned row is read once, and should not push the
+// candidate rows the regular steps read out of L2.
 template <int TW, bool GREEDY, bool RECIP>
 __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, const Tabu<TW> &tb,
                                         int lane, uint32_t t, uint32_t ant, uint32_t it,
@@ -137,7 +139,7 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, co
             const uint32_t word = tb.word_of(vq);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
             // a chunk whose four nodes are visited is not read
-            w4[u] = (c < nch && bits[u] != 0xFu) ? *reinterpret_cast<const float4 *>(row + v0)
+            w4[u] = (c < nch && bits[u] != 0xFu) ? __ldcs(reinterpret_cast<const float4 *>(row + v0))
                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
@@ -213,7 +215,7 @@ __device__ __forceinline__ int scan_unvisited(const float *__restrict__ row, int
         if (!__any_sync(FULL, vs[0] >= 0)) break;
         float x[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) x[u] = vs[u] >= 0 ? row[vs[u]] : 0.0f;
+        for (int u = 0; u < U; ++u) x[u] = vs[u] >= 0 ? __ldcs(row + vs[u]) : 0.0f;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (vs[u] < 0) continue;
@@ -525,7 +527,7 @@ __device__ __forceinline__ void row_tour_pipelined(const ConstructArgs &a, const
             const int v0 = c << 2;
             const uint32_t word = tb.word_of(v0 < n ? v0 : n - 1);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
-            w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            w4[u] = c < nch ? __ldcs(reinterpret_cast<const float4 *>(row + v0)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         row_draws<U>(nch, lane, (uint32_t)(t + 1), (uint32_t)ant, it, a.key0, a.key1, ln);
         uint32_t bk = 0u, bv = 0xFFFFFFFFu;
@@ -665,8 +667,9 @@ __device__ __forceinline__ bool stage_table(unsigned char *s_w, const void *src_
 // STAGED: 0 the table is read from global memory; 1 it is staged whole; 2
 // its first a.stage_rows rows are staged (candidate-list mode).  MAXT: threads
 // a CTA may have -- 384 (12 warps, registers for the four-step groups) or,
-// for tables mostly too large to stage, 1024 (32 warps with fewer registers
-// each: the dependent row reads from L2 are hidden by more ants per SM).
+// for tables mostly too large to stage, 512, 768 or 1024 (up to 32 warps with
+// fewer registers each: the dependent row reads from L2 are hidden by more
+// ants per SM).
 template <int MODE, int STAGED, int TW, int MAXT = 384>
 __global__ void __launch_bounds__(MAXT, 1) k_construct(const ConstructArgs a, int cons_warps)
 {
@@ -1174,7 +1177,13 @@ KernelFn pick_kernel(int mode, int staged, int tw)
 }
 
 // the 32-warp form, tabus in shared memory, rows read through L1 and L2
-KernelFn pick_kernel_wide(int) { return k_construct<CAND, 0, 0, 1024>; }
+// The smallest of the 512-, 768- and 1024-thread builds that holds `warps`
+// warps (fewer threads a CTA leave more registers a thread).
+KernelFn pick_kernel_wide(int warps)
+{
+    return warps <= 16 ? k_construct<CAND, 0, 0, 512>
+                       : (warps <= 24 ? k_construct<CAND, 0, 0, 768> : k_construct<CAND, 0, 0, 1024>);
+}
 
 KernelFn pick_kernel_long(int tw)
 {
@@ -1251,7 +1260,13 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
     if (plan->wide) {
         // no staging: shared memory holds only the tabus, which leaves L1 room
         // to cache the candidate rows (measured faster than staging the few
-        // rows that fit: 84 -> 69 ms at n = 18,500)
+        // rows that fit: 84 -> 69 ms at n = 18,500).  The ants run in rounds of
+        // one per warp; the fewest rounds that 32 warps a CTA need are filled
+        // evenly, so the last round is not a nearly idle one (n = m = 10,000:
+        // 22 warps, 3 full rounds, 22.6 -> 18.4 ms)
+        const int per_round = num_sms * 32;
+        const int rounds = (a.m + per_round - 1) / per_round;
+        w = (a.m + num_sms * rounds - 1) / (num_sms * rounds);
         plan->staged = 0;
         plan->cons_warps = w;
         plan->gen_warps = 0;
@@ -1281,7 +1296,7 @@ cudaError_t plan_construct(const ConstructArgs &a, int num_sms, size_t smem_opti
         plan->smem = (size_t)4 * per_warp;
     }
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan->staged, plan->tw)
-                     : (plan->wide ? pick_kernel_wide(plan->staged)
+                     : (plan->wide ? pick_kernel_wide(plan->cons_warps)
                                    : pick_kernel(row ? ROW : CAND, plan->staged, plan->tw));
     return cudaFuncSetAttribute(reinterpret_cast<const void *>(k),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
@@ -1324,7 +1339,7 @@ cudaError_t launch_construct(const ConstructArgs &a, const ConstructPlan &plan, 
     const bool var = a.cl == 0 && (a.sel != 0 || a.ct != 0);
     KernelFn k = var ? pick_kernel_var(a.sel, a.ct, plan.staged, plan.tw)
                      : plan.longl ? pick_kernel_long(plan.tw)
-                     : (plan.wide ? pick_kernel_wide(plan.staged)
+                     : (plan.wide ? pick_kernel_wide(plan.cons_warps)
                                   : pick_kernel(a.cl == 0 ? ROW : CAND, plan.staged, plan.tw));
     k<<<plan.grid, (plan.cons_warps + plan.gen_warps) * 32, plan.smem, s>>>(b, plan.cons_warps);
     return cudaGetLastError();

@@ -200,17 +200,21 @@ def test_greedy_fallback_on_a_converged_trail_matches_oracle(n, cl, kind):
     g.close()
 
 
-@pytest.mark.parametrize("n,cl,kind,m,fallback,trail", [
-    (10000, 16, "clustered", 4901, 0, "deposits"),
-    (12000, 16, "uniform", 4950, 1, "deposits"),
-    (9500, 16, "uniform", 4903, 0, "converged"),
+@pytest.mark.parametrize("n,cl,kind,m,fallback,trail,block", [
+    # 2 rounds of 17 warps (the 768-thread build), warps loop over ants
+    (10000, 16, "clustered", 4901, 0, "deposits", 17 * 32),
+    # 2 rounds of 30 warps (the 1024-thread build)
+    (12000, 16, "uniform", 9000, 1, "deposits", 30 * 32),
+    # 1 round of 14 warps (the 512-thread build)
+    (9500, 16, "uniform", 2000, 0, "converged", 14 * 32),
 ])
-def test_many_ants_on_long_tours_match_oracle(n, cl, kind, m, fallback, trail):
+def test_many_ants_on_long_tours_match_oracle(n, cl, kind, m, fallback, trail, block):
     """Tables mostly too large to stage (under a quarter fits beside the tabus)
-    and many ants: the construction runs 32 warps per CTA with shared-memory
-    tabus.  After deposits on long random
-    tours, or on a converged-looking trail, fallbacks of every kind run;
-    sampled ants, the last ones included, match the oracle pick for pick."""
+    and many ants: the construction runs up to 32 warps per CTA with
+    shared-memory tabus, as many as fill the fewest rounds of one ant a warp
+    evenly.  After deposits on long random tours, or on a converged-looking
+    trail, fallbacks of every kind run; sampled ants, the last ones included,
+    match the oracle pick for pick."""
     xy = I.clustered(n, 80 + n) if kind == "clustered" else I.uniform(n, 80 + n)
     g, o = _pair(xy=xy, m=m, cl=cl, rho=0.05, seed=11, fallback=fallback)
     d = o.state()["d"]
@@ -243,9 +247,9 @@ def test_many_ants_on_long_tours_match_oracle(n, cl, kind, m, fallback, trail):
     g.construct()
     tours, lens = g.tours()
     st = g.stats()
-    assert st["construct_block"] == 1024
+    assert st["construct_block"] == block and st["construct_staged"] == 0
     assert np.array_equal(np.sort(tours, axis=1), np.broadcast_to(np.arange(n, dtype=np.int32), (m, n)))
-    sample = list(range(0, m, 150)) + [m - 2, m - 1]
+    sample = list(range(0, m, m // 32)) + [m - 2, m - 1]
     kinds = [check_ant(o, it, k, tours[k], lens[k]) for k in sample]
     near = kinds.count("near_tie")
     print(f"n={n} cl={cl} m={m} fallback={fallback} {trail}: {st['fallback_steps']} fallbacks "
@@ -441,7 +445,8 @@ def test_full_size_n1000_cl32_sampled_parity():
 
 def test_learned_prior_race_shape_n18500_cl16_sampled_parity():
     """The largest race workload's colony shape (uniform n = 18,500, m = n,
-    cl = 16): 32 warps per CTA read the candidate rows through L1 and L2, the
+    cl = 16): 31 warps per CTA (four full rounds of one ant a warp) read the
+    candidate rows through L1 and L2, the
     tabus live in shared memory, and late-tour fallbacks read only the
     unvisited nodes.  Every tour is a permutation with an exact length; 25
     sampled ants match the oracle pick for pick in iteration 0 and, after the
@@ -464,7 +469,7 @@ def test_learned_prior_race_shape_n18500_cl16_sampled_parity():
         o.update(tours[ib], int(lens[ib]))
         del tours
     st = g.stats()
-    assert st["construct_staged"] == 0 and st["construct_block"] == 1024 and st["iterations"] == 2
+    assert st["construct_staged"] == 0 and st["construct_block"] == 31 * 32 and st["iterations"] == 2
     print(f"n=18500 sampled ants: {kinds.count('exact')} exact, {kinds.count('near_tie')} near-tie; "
           f"fallbacks {st['fallback_steps']}, row scans {st['fallback_scans']}")
     tau, tmin, tmax = g.pheromone()
