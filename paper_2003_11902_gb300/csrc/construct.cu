@@ -117,9 +117,12 @@ __device__ __forceinline__ float pick_f(const float4 &r, int e)
 // fallback on choice_info); otherwise the reservoir key log2(r) * inv-weight,
 // r from the whole-row stream, with `row` holding the reciprocal weights (RECIP)
 // or the weights.  Eight chunk-columns (1024 nodes) are loaded before use, so
-// rows of up to 1024 nodes cost one memory round trip.  The loads are
-// streaming (evict-first): a scanned row is read once, and should not push the
-// candidate rows the regular steps read out of L2.
+// rows of up to 1024 nodes cost one memory round trip.  The fallback scans
+// (!RECIP: `row` is a row of choice_info in global memory) use streaming
+// loads (evict-first): a scanned row is read once, and should not push the
+// candidate rows the regular steps read out of L2.  The whole-row steps
+// (RECIP) use generic loads: their table may be staged in shared memory, which
+// a global-space load must not be given.
 template <int TW, bool GREEDY, bool RECIP>
 __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, const Tabu<TW> &tb,
                                         int lane, uint32_t t, uint32_t ant, uint32_t it,
@@ -139,8 +142,11 @@ __device__ __forceinline__ int scan_row(const float *__restrict__ row, int n, co
             const uint32_t word = tb.word_of(vq);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
             // a chunk whose four nodes are visited is not read
-            w4[u] = (c < nch && bits[u] != 0xFu) ? __ldcs(reinterpret_cast<const float4 *>(row + v0))
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *src = reinterpret_cast<const float4 *>(row + v0);
+            if (c < nch && bits[u] != 0xFu)
+                w4[u] = RECIP ? *src : __ldcs(src);
+            else
+                w4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -527,7 +533,8 @@ __device__ __forceinline__ void row_tour_pipelined(const ConstructArgs &a, const
             const int v0 = c << 2;
             const uint32_t word = tb.word_of(v0 < n ? v0 : n - 1);
             bits[u] = c < nch ? (word >> (v0 & 31)) & 0xFu : 0xFu;
-            w4[u] = c < nch ? __ldcs(reinterpret_cast<const float4 *>(row + v0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            // generic load: the table may be staged in shared memory
+            w4[u] = c < nch ? *reinterpret_cast<const float4 *>(row + v0) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         row_draws<U>(nch, lane, (uint32_t)(t + 1), (uint32_t)ant, it, a.key0, a.key1, ln);
         uint32_t bk = 0u, bv = 0xFFFFFFFFu;
