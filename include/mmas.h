@@ -84,8 +84,8 @@ typedef struct {
  *            iteration best; 2 2-opt every ant's tour.  Bentley's 2-opt with
  *            the candidate lists as neighbour lists and don't-look bits, first
  *            improvement, cities visited in index order, runs repeated until
- *            one makes no move.  Needs cl >= 1 and 12.125n bytes + 2 KB of
- *            shared memory per CTA (n <= 19,000 on GB300)             (0)
+ *            one makes no move.  Needs cl >= 1 and 12.125n bytes + 2.25 KB
+ *            of shared memory per CTA (n <= 18,979 on GB300)          (0)
  *   selection  whole-row mode (cl = 0) only: 0 weighted reservoir sampling
  *            (Alg. 4); 1 the parallel roulette wheel (Sec. 4.2.1), one draw
  *            per step, the exact single-precision procedure described below (0)

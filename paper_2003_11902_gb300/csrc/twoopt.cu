@@ -30,6 +30,22 @@
 // clustered n = 3800 workload), the two new edges, the four cleared bits --
 // while the other warps wait at the barrier.
 //
+// Several moves a round.  A search reads the tour only at the positions of
+// its city and of its neighbours, and one step either side of them (its
+// footprint).  A move rewrites positions pa - 1 .. pb + 1 only (the reversed
+// path [pa..pb] and the two edges that border it).  So a search whose
+// footprint lies outside pa - 2 .. pb + 2 returns the same result on the new
+// tour as on the old one.  The window's first cities (one a warp) keep their
+// footprints; after the search every warp tests its city's footprint against
+// the ranges of the moves of the earlier kept cities (computed from their
+// move records, which stay exact for every move that is applied), and warp 0
+// walks on from the round's first move: a city whose footprint misses every
+// move applied so far keeps its result -- no move: its bit is set; a move: it
+// is applied next; a city skipped for its bit: its bit stays set -- and the
+// walk stops at the first city it cannot vouch for, where the next round
+// starts.  That is again the sequential search move for move; on the
+// clustered n = 3800 workload it takes about a third of the rounds.
+//
 // Neighbour lists are the colony's candidate lists.  For the iteration-best
 // tour (one CTA) the coordinates and 16-bit lists are staged in shared memory
 // when they fit, so a neighbour costs shared loads only; otherwise neighbour
@@ -152,11 +168,15 @@ __device__ __forceinline__ bool nint_sqrt_below(long long s, long long t)
 // with d(c1, c2) below that radius, and its first improving one is the lowest
 // such lane whose gain is positive.  The successor side wins over the
 // predecessor side.  Every lane returns the same result.
+// fp (when not null) receives the footprint's positions: p = pos[c1] in
+// fp[0], and pos of neighbour h in fp[1 + h].
 template <bool XY, bool STAGED>
 __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geometry<XY, STAGED> &g,
-                                               const TourView &tv, int c1, int lane, Move &mv)
+                                               const TourView &tv, int c1, int lane, Move &mv,
+                                               uint16_t *fp)
 {
     const int p = tv.pos[c1];
+    if (fp && lane == 0) fp[0] = (uint16_t)p;
     const int pn = tv.nxt(p), pp = tv.prv(p);
     const int s1 = tv.tour[pn], p1 = tv.tour[pp];
     const int rs = tv.edge[p], rp = tv.edge[pp];
@@ -166,6 +186,7 @@ __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geomet
         const int c2 = g.neighbour(c1, lane);
         d12 = g.neighbour_dist(c1, lane, c2);
         q = tv.pos[c2];
+        if (fp) fp[1 + lane] = (uint16_t)q;
         const int qn = tv.nxt(q), qp = tv.prv(q);
         tn = tv.tour[qn];
         tp = tv.tour[qp];
@@ -199,8 +220,6 @@ __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geomet
     return true;
 }
 
-// Cities in the first window after a move.
-constexpr int FIRST_WINDOW = 8;
 
 // Reverse tour[pa..pb] (len cities, cyclic) with `count` threads numbered
 // `t`; the len - 1 edges inside the path reverse with it.
@@ -264,9 +283,11 @@ __device__ __forceinline__ void finish_move(const TourView &tv, uint32_t *dlb, c
 
 // One warp applies move mv: the window's cities before mv.c1 get
 // their bits set, then the shorter of the two paths between the removed edges
-// is reversed and the move's edges and bits are updated.
-__device__ __forceinline__ void apply_move(const TourView &tv, uint32_t *dlb, const Move &mv,
-                                           int l, int lane)
+// is reversed and the move's edges and bits are updated.  Returns the first
+// position of the reversed path and sets len to its length; the warp has
+// synchronised, so every lane sees the finished move.
+__device__ __forceinline__ int apply_move(const TourView &tv, uint32_t *dlb, const Move &mv, int l,
+                                          int lane, int &len_out)
 {
     const int n = tv.n;
     dlb_set_range(dlb, l, mv.c1, lane, 32);
@@ -287,6 +308,106 @@ __device__ __forceinline__ void apply_move(const TourView &tv, uint32_t *dlb, co
     reverse_path(tv, pa, pb, len, lane, 32);
     __syncwarp();
     if (lane == 0) finish_move(tv, dlb, mv, pa, pb);
+    __syncwarp();
+    len_out = len;
+    return pa;
+}
+
+// Cities of a window whose search results (and footprints) are kept: the
+// first city of each of the first MM_MAX warps.
+constexpr int MM_MAX = 16;
+// Moves one round may apply (their changed ranges are held in registers).
+constexpr int MR_MAX = 8;
+
+// Search results of the window's first cities, kept for the walk: res 0 = the
+// city's bit was set (not searched), 1 = no move, 2 = a move (in the warp's
+// move slot); fp = the footprint (find_move_warp).
+struct RoundKeep {
+    uint16_t fp[MM_MAX][33];
+    int32_t res[MM_MAX];
+    uint32_t hit[MM_MAX];  // bit i: the move of kept city i changes this city's footprint
+    int32_t next, moves;
+};
+
+// The positions a move rewrites, widened by the footprint's one step: the
+// reversed path [pa..pb] is the shorter one, as apply_move chooses it, and the
+// range is pa - 2 .. pb + 2 (start ra, length rl, cyclic).
+__device__ __forceinline__ void move_range(const Move &mv, int n, int &ra, int &rl)
+{
+    const int p = mv.p, q = mv.q;
+    int pa, pb, ca;
+    if (mv.side == 0) {
+        pa = p + 1 == n ? 0 : p + 1; pb = q; ca = q + 1 == n ? 0 : q + 1;
+    } else {
+        pa = q; pb = p == 0 ? n - 1 : p - 1; ca = p;
+    }
+    int len = pb - pa + 1;
+    if (len <= 0) len += n;
+    if (2 * len > n) {
+        pa = ca;
+        len = n - len;
+    }
+    ra = pa >= 2 ? pa - 2 : pa - 2 + n;
+    rl = len + 4 < n ? len + 4 : n;
+}
+
+// Warp j of the window (its kept city l + j): which moves of the earlier kept
+// cities change its footprint (a skipped city's footprint is its own
+// position: a move that clears its bit rewrites that position).
+__device__ __forceinline__ uint32_t keep_hits(const RoundKeep &kp, const Move *s_move, int j, int k,
+                                              int n, int lane)
+{
+    const int res = kp.res[j];
+    const int p = kp.fp[j][0];  // every lane tests the city's own position (k may be 32)
+    const int x = (res != 0 && lane < k) ? kp.fp[j][1 + lane] : p;
+    uint32_t mask = 0;
+    for (int i = 0; i < j; ++i) {
+        if (kp.res[i] != 2) continue;
+        int ra, rl;
+        move_range(s_move[i], n, ra, rl);
+        int dx = x - ra, dp = p - ra;
+        if (dx < 0) dx += n;
+        if (dp < 0) dp += n;
+        if (__any_sync(0xFFFFFFFFu, dx < rl || dp < rl)) mask |= 1u << i;
+    }
+    return mask;
+}
+
+// Warp 0, after the round whose lowest improving city is `first` (window
+// cities from l; cities below lim were each kept by warp c - l): apply that
+// move, then walk on through first + 1 .. lim - 1 while the kept results
+// hold (no hit from a move applied so far).  Returns the next city to search
+// and sets moves.
+__device__ __forceinline__ int apply_moves(const TourView &tv, uint32_t *dlb, const Move *s_move,
+                                           const RoundKeep &kp, int l, int first, int lim, int NW,
+                                           int lane, int &moves)
+{
+    int len = 0;
+    apply_move(tv, dlb, s_move[(first - l) & (NW - 1)], l, lane, len);
+    if (first >= lim) {
+        moves = 1;
+        return first + 1;
+    }
+    uint32_t applied = 1u << (first - l);
+    int nr = 1;
+    int c = first + 1;
+    for (; c < lim; ++c) {
+        const int j = c - l;
+        if (kp.hit[j] & applied) break;
+        const int res = kp.res[j];
+        if (res == 0) continue;  // its bit, set before, was not cleared
+        if (res == 1) {          // no move on the new tour either
+            if (lane == 0) dlb[c >> 5] |= 1u << (c & 31);
+            __syncwarp();
+            continue;
+        }
+        if (nr == MR_MAX) break;
+        apply_move(tv, dlb, s_move[j], c, lane, len);
+        applied |= 1u << j;
+        ++nr;
+    }
+    moves = nr;
+    return c;
 }
 
 template <bool XY, bool STAGED, bool IB>
@@ -295,6 +416,8 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, tid = threadIdx.x, W = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, NW = W >> 5;
+    // cities in the first window after a move: one a warp, as far as results are kept
+    const int first_window = NW < MM_MAX ? NW : MM_MAX;
     const Layout L = Layout::make(n, a.k, STAGED);
     TourView tv;
     tv.n = n;
@@ -307,6 +430,8 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                                  reinterpret_cast<const uint16_t *>(smem + L.nn)};
     __shared__ int s_first[3];
     __shared__ Move s_move[32];  // per warp
+    __shared__ RoundKeep s_keep;
+    const int mm = NW < MM_MAX ? NW : MM_MAX;  // window cities whose results are kept
     __shared__ int s_red[32];
     __shared__ unsigned long long s_best;
 
@@ -363,14 +488,24 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
             while (improved && !capped) {  // passes
                 improved = false;
                 int l = 0;
-                int w = FIRST_WINDOW;  // cities in the window; doubles while none has a move
+                int w = first_window;  // cities in the window; doubles while none has a move
                 while (l < n) {  // windows
                     const int wend = l + w < n ? l + w : n;
                     int mine = INT_MAX;
                     for (int c1 = l + warp; c1 < wend; c1 += NW) {  // warp-uniform
-                        if (dlb_get(s_dlb, c1)) continue;
+                        const bool keep = c1 == l + warp && warp < mm;
+                        if (dlb_get(s_dlb, c1)) {
+                            if (keep && lane == 0) {
+                                s_keep.res[warp] = 0;
+                                s_keep.fp[warp][0] = (uint16_t)tv.pos[c1];
+                            }
+                            continue;
+                        }
                         Move mv;
-                        if (find_move_warp<XY, STAGED>(a, g, tv, c1, lane, mv)) {
+                        const bool found = find_move_warp<XY, STAGED>(a, g, tv, c1, lane, mv,
+                                                                      keep ? s_keep.fp[warp] : nullptr);
+                        if (keep && lane == 0) s_keep.res[warp] = found ? 2 : 1;
+                        if (found) {
                             if (lane == 0) s_move[warp] = mv;
                             mine = c1;
                             break;
@@ -391,13 +526,32 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                     // cities [l, first) were evaluated without a move (every warp
                     // stopped at its own first move, so all of them were reached);
                     // city c was searched by warp (c - l) mod NW
-                    if (warp == 0) apply_move(tv, s_dlb, s_move[(first - l) & (NW - 1)], l, lane);
+                    const int lim = wend < l + mm ? wend : l + mm;
+                    if (first < lim) {  // the kept cities after first: hits, one warp each
+                        const int j = warp;
+                        if (l + j > first && l + j < lim) {
+                            const uint32_t h = keep_hits(s_keep, s_move, j, a.k, n, lane);
+                            if (lane == 0) s_keep.hit[j] = h;
+                        }
+                        __syncthreads();
+                    }
+                    if (warp == 0) {
+                        int moves = 0;
+                        const int next = apply_moves(tv, s_dlb, s_move, s_keep, l, first, lim, NW,
+                                                     lane, moves);
+                        if (lane == 0) {
+                            s_keep.next = next;
+                            s_keep.moves = moves;
+                        }
+                    }
                     improved = true;
-                    ++run_moves;
-                    l = first + 1;
-                    w = FIRST_WINDOW;
                     __syncthreads();
-                    if (++total > cap) {
+                    const int moves = s_keep.moves;
+                    run_moves += moves;
+                    l = s_keep.next;
+                    w = first_window;
+                    total += moves;
+                    if (total > cap) {
                         if (tid == 0) atomicOr(a.err, ERR_LS_CAP);
                         capped = true;
                         break;
@@ -453,7 +607,9 @@ size_t two_opt_smem(int n, int k, bool staged) { return Layout::make(n, k, stage
 
 bool two_opt_fits(int n, int k, bool staged, size_t smem_optin)
 {
-    return two_opt_smem(n, k, staged) + 2048 <= smem_optin;
+    // + the kernel's static shared memory (move slots, the kept search
+    // results, reduction words: 2,048 bytes) with room to spare
+    return two_opt_smem(n, k, staged) + 2304 <= smem_optin;
 }
 
 cudaError_t launch_neighbour_dist(const TwoOptArgs &a, int32_t *nnd, cudaStream_t s)
