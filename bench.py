@@ -60,6 +60,9 @@ WORKLOADS = {
     # construction at large n
     "uniform-n5000-cl16": dict(n=5000, m=5000, cl=16, kind="uniform", iseed=1005),
     "uniform-n18500-cl16": dict(n=18500, m=18500, cl=16, kind="uniform", iseed=1018),
+    # the same construction form as n = 18,500 (32 warps a CTA, nothing staged) at a size whose
+    # matrices (4 x 0.4 GB) a full ncu capture can save and restore
+    "uniform-n10000-cl16": dict(n=10000, m=10000, cl=16, kind="uniform", iseed=1010),
     # 256 uniform instances, n = round(exp(U[ln 100, ln 2000])) (size seed 1000), coordinate
     # seed 1000 + i, m = n each
     "batched-256-n100-2000-cl32": dict(kind="batched", count=256, lo=100, hi=2000, cl=32,
@@ -80,7 +83,7 @@ DEFAULT_STEPS = {"uniform-n1000-cl32": 1000, "uniform-n200-fullrow": 1000,
                  "uniform-n200-fullrow-rwm": 1000, "uniform-n200-fullrow-rwm-ct": 1000,
                  "uniform-n200-fullrow-ct": 1000,
                  "clustered-n3800-cl16-2opt": 100, "batched-256-n100-2000-cl32": 30,
-                 "uniform-n5000-cl16": 100, "uniform-n18500-cl16": 20,
+                 "uniform-n5000-cl16": 100, "uniform-n18500-cl16": 20, "uniform-n10000-cl16": 50,
                  "learned-prior-n1000-cl16-2opt": 200, "learned-prior-n5000-cl16-2opt": 30,
                  "learned-prior-n18500-cl16-2opt": 10}
 PARAMS = dict(alpha=1.0, beta=2.0, rho=0.02, p_best=0.01)
