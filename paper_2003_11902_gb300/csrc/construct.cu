@@ -273,7 +273,8 @@ __device__ __forceinline__ void reach_entry(uint2 e, bool in, const Tabu<TW> &tb
 template <int TW>
 __device__ __forceinline__ int greedy_reach(const uint2 *__restrict__ xl, const float *__restrict__ xb,
                                             int xe, const uint2 *__restrict__ xx, const int32_t *xn,
-                                            const Tabu<TW> &tb, int lane)
+                                            const Tabu<TW> &tb, int lane, uint32_t &mx_out,
+                                            uint32_t &v_out)
 {
     constexpr int P = REACH_MAX / 32;
     uint2 e[P];
@@ -288,8 +289,63 @@ __device__ __forceinline__ int greedy_reach(const uint2 *__restrict__ xl, const 
     for (int p = 0; p < P; ++p) reach_entry<TW>(e[p], lane + 32 * p < xe, tb, bk, bv);
     if (nx > 0) reach_entry<TW>(ex, lane < nx, tb, bk, bv);
     const uint32_t mx = __reduce_max_sync(FULL, bk);
+    const uint32_t v = __reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+    mx_out = mx;  // the lists' best (key 0: none unvisited) for the far list
+    v_out = v;
     if (mx <= kb) return -1;  // no unvisited listed node, or one outside may be as good
-    return (int)__reduce_min_sync(FULL, bk == mx ? bv : 0xFFFFFFFFu);
+    return (int)v;
+}
+
+// The far list, when the reach list could not decide: the unvisited nodes
+// among the row's nearest REACH_FAR (entries REACH_MAX .. of xf: REACH_FAR -
+// REACH_MAX ids, two to a 32-bit word) have their choice_info read from the
+// row (global memory) and join the lists' best (mx, v); when that beats the
+// bound on every node beyond the far list strictly, it is the row's greedy
+// choice (ties -> lower id; every node of the largest choice_info is listed),
+// else -1.  Three memory round trips: every lane's ids at once, then the
+// choice_info of half of them at a time.
+template <int TW>
+__device__ __forceinline__ int greedy_far(const float *__restrict__ row, const uint16_t *__restrict__ xf,
+                                          const float *__restrict__ xfb, const Tabu<TW> &tb, int lane,
+                                          uint32_t mx, uint32_t v)
+{
+    constexpr int W = (REACH_FAR - REACH_MAX) / 64;  // words a lane: 14
+    constexpr int H = W / 2;                         // words a half
+    const uint32_t *xw = reinterpret_cast<const uint32_t *>(xf);  // 4-byte aligned
+    uint32_t w[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) w[u] = __ldg(xw + u * 32 + lane);
+    uint32_t bk = mx, bv = v;  // the same in every lane
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t node[2 * H];
+        uint32_t okm = 0;
+#pragma unroll
+        for (int u = 0; u < H; ++u) {
+            node[2 * u] = w[half * H + u] & 0xFFFFu;
+            node[2 * u + 1] = w[half * H + u] >> 16;
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * H; ++q) {
+            const uint32_t word = tb.word_of((int)node[q]);  // every lane calls it
+            okm |= ((word >> (node[q] & 31)) & 1u) ? 0u : (1u << q);
+        }
+        float x[2 * H];
+#pragma unroll
+        for (int q = 0; q < 2 * H; ++q) x[q] = ((okm >> q) & 1u) ? __ldcs(row + node[q]) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2 * H; ++q) {
+            const uint32_t k = ((okm >> q) & 1u) ? (__float_as_uint(x[q]) | 0x80000000u) : 0u;  // choice_info >= 0
+            if (k > bk || (k == bk && k != 0u && node[q] < bv)) {
+                bk = k;
+                bv = node[q];
+            }
+        }
+    }
+    const uint32_t kb = __float_as_uint(*xfb) | 0x80000000u;
+    const uint32_t m2 = __reduce_max_sync(FULL, bk);
+    if (m2 <= kb) return -1;
+    return (int)__reduce_min_sync(FULL, bk == m2 ? bv : 0xFFFFFFFFu);
 }
 
 // Bit set in a fallback's result when the whole row was scanned.
@@ -309,13 +365,19 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
                                           int lane, int mode, uint32_t t, uint32_t ant, uint32_t it,
                                           uint32_t k0, uint32_t k1, uint32_t *err, int cur,
                                           const uint2 *xl, const float *xb, const uint2 *xx,
-                                          const int32_t *xn, int xe)
+                                          const int32_t *xn, int xe, const uint16_t *xf, int fe,
+                                          const float *xfb)
 {
     const bool sparse = TW == 0 && n - (int)t <= SPARSE_SCAN_MAX;  // few nodes left: read only those
     if (mode == 0) {
         if (xe > 0) {
-            const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane);
+            uint32_t mx, v;
+            const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane, mx, v);
             if (r >= 0) return r;
+            if (fe > 0 && !sparse) {
+                const int r2 = greedy_far<TW>(row, xf, xfb, tb, lane, mx, v);
+                if (r2 >= 0) return r2;
+            }
         }
         if (sparse) return scan_unvisited<true>(row, n, tb.w, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
         return scan_row<TW, true, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
@@ -369,7 +431,8 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
                                             (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
                                             cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
+                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
                           fbn);
 }
 
@@ -473,7 +536,8 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
             cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                               (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                               a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
+                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
             fbn);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
@@ -744,7 +808,8 @@ __device__ __forceinline__ int cand_step2(const ConstructArgs &a, const Tabu<TW>
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                                             (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                                             a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
+                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
                           fbn);
 }
 

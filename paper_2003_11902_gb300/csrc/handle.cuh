@@ -37,6 +37,9 @@ struct mmas_handle {
     uint2 *xxw = nullptr;            // [n][REACH_EXTRA]
     int32_t *xxn = nullptr;          // [n]
     int32_t *xhot = nullptr;         // [n]
+    int32_t fe = 0, fp = 0;          // far list of the greedy fallback: entries past the reach list, row pitch
+    uint16_t *xf16 = nullptr;        // [n][fp]
+    float *xfb = nullptr;            // [n]
     mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
     int32_t *h_tour = nullptr;      // pinned staging of the best tour
 

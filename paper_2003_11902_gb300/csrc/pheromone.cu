@@ -197,9 +197,14 @@ template <bool FULLROW, bool ALPHA1, bool EXTRAS>
 __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float tmin, float tmax,
                                                float delta)
 {
-    __shared__ uint32_t s_bound[8], s_ball[8];
+    __shared__ uint32_t s_bound[8], s_ball[8], s_bfar[8];
     __shared__ int s_nx, s_hot[8];
     const bool reach = !FULLROW && a.xe > 0;
+    // far list: the bound covers every node j != i with eta^beta_ij at most that
+    // of the row's last far node (every node beyond the list)
+    const bool far = reach && a.fe > 0;
+    const float thr_far = far ? __ldg(a.eb + (size_t)i * a.ld + a.xf16[(size_t)i * a.fp + a.fp - 1]) : -1.0f;
+    float bound_far = 0.0f;
     // the extra list (xhot set) is filled only for rows that had few nodes
     // above the trail floor outside the list at the last pass (that changes
     // slowly); the others just count theirs
@@ -266,6 +271,7 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
                 }
                 if (!stored) bound = fmaxf(bound, w);
                 if (EXTRAS) bound_all = fmaxf(bound_all, w);
+                if (far && ev[c] <= thr_far) bound_far = fmaxf(bound_far, w);
             }
         }
         trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
@@ -275,6 +281,10 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
         if (reach) {  // choice_info >= 0: its bits order like the values
             const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
             if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = wmax;
+            if (far) {
+                const uint32_t fmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_far));
+                if ((threadIdx.x & 31) == 0) s_bfar[threadIdx.x >> 5] = fmax;
+            }
             if (extras) {
                 const uint32_t amax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_all));
                 const int hots = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)hot_cnt);
@@ -312,6 +322,11 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
                 a.xlb[i] = __uint_as_float(all || !extras ? m : ma);
                 a.xxn[i] = all ? hots : 0;
                 if (extras) a.xhot[i] = hots;
+                if (far) {
+                    uint32_t mf = 0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mf = s_bfar[w] > mf ? s_bfar[w] : mf;
+                    a.xfb[i] = __uint_as_float(mf);
+                }
             }
             __syncthreads();  // s_bound is read before the CTA's next row writes it
         }
@@ -344,7 +359,11 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
     const float thr = (reach && a.xe < a.n - 1)
                           ? __ldg(a.eb + (size_t)i * a.ld + a.xl32[(size_t)i * a.xe + a.xe - 1])
                           : -1.0f;
-    float bound = 0.0f, bound_all = 0.0f;
+    // far list: the bound covers every node j != i with eta^beta_ij at most that
+    // of the row's last far node (every node beyond the list)
+    const bool far = reach && a.fe > 0;
+    const float thr_far = far ? __ldg(a.eb + (size_t)i * a.ld + a.xf16[(size_t)i * a.fp + a.fp - 1]) : -1.0f;
+    float bound = 0.0f, bound_all = 0.0f, bound_far = 0.0f;
     int hot_cnt = 0, nx = 0;  // nx: extras stored so far (the same in every lane)
     const unsigned below = (1u << lane) - 1u;
     const int nq = a.ld >> 2;
@@ -411,6 +430,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
                 }
                 if (outside && !stored) bound = fmaxf(bound, w);
                 if (EXTRAS && outside) bound_all = fmaxf(bound_all, w);
+                if (far && outside && ev[c] <= thr_far) bound_far = fmaxf(bound_far, w);
             }
         }
         if (inq) {
@@ -434,6 +454,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
             const uint32_t m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
             const uint32_t ma = extras ? __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_all)) : 0u;
             const int hots = extras ? (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)hot_cnt) : 0;
+            const uint32_t mf = far ? __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_far)) : 0u;
             if (lane == 0) {
                 // every node above the floor stored: the extra list is exact and
                 // the bound covers the rest; else the list is unused (without
@@ -442,6 +463,7 @@ __device__ __forceinline__ void update_row(const UpdateArgs &a, int i, float tmi
                 a.xlb[i] = __uint_as_float(all || !extras ? m : ma);
                 a.xxn[i] = all ? hots : 0;
                 if (extras) a.xhot[i] = hots;
+                if (far) a.xfb[i] = __uint_as_float(mf);
             }
         }
     }

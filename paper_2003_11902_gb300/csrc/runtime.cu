@@ -73,7 +73,8 @@ void free_all(mmas_handle *h)
     void *bufs[] = {h->xy,      h->dist,   h->eb,      h->tau,     h->wmat, h->cwinv,
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
                     h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->ext_bad, h->nnd,
-                    h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot};
+                    h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot,
+                    h->xf16,    h->xfb};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -298,6 +299,15 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
         CK(h, dalloc(&h->xxn, (size_t)n * sizeof(int32_t), h->stream));
         CK(h, dalloc(&h->xhot, (size_t)n * sizeof(int32_t), h->stream));
         CK(h, launch_candidates(h->dist, n, ld, h->xe, h->xl32, nullptr, s));
+        // large rows: the far list (the nearest REACH_FAR nodes, 16-bit ids) and
+        // its bound decide most fallbacks the reach list cannot
+        if (n >= REACH_FAR_MIN_N) {
+            h->fp = REACH_FAR;
+            h->fe = REACH_FAR - REACH_MAX;
+            CK(h, dalloc(&h->xf16, (size_t)n * h->fp * sizeof(uint16_t), h->stream));
+            CK(h, dalloc(&h->xfb, (size_t)n * sizeof(float), h->stream));
+            CK(h, launch_candidates(h->dist, n, ld, h->fp, nullptr, h->xf16, s));
+        }
     }
     CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, s));
     CK(h, launch_init_colony(n, ld, (double)h->p.rho, h->p_root, h->tau, h->sc, s));
@@ -318,6 +328,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
     ca.tours = h->tours; ca.sc = h->sc;
     ca.xe = h->xe; ca.xlw = h->xlw; ca.xlb = h->xlb; ca.xxw = h->xxw; ca.xxn = h->xxn;
+    ca.fe = h->fe; ca.fp = h->fp; ca.xf16 = h->xf16; ca.xfb = h->xfb;
     ca.stage_w_bytes = (uint32_t)cw_bytes;
     ca.stage_c_bytes = (uint32_t)cc_bytes;
     if (cl == 0) { ca.stage_w_bytes = 0; ca.stage_c_bytes = 0; }
@@ -353,6 +364,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ua.nbr = h->nbr; ua.sc = h->sc;
     ua.xe = h->xe; ua.xl32 = h->xl32; ua.xlw = h->xlw; ua.xlb = h->xlb; ua.xxw = h->xxw; ua.xxn = h->xxn;
     ua.xhot = h->xhot;
+    ua.fe = h->fe; ua.fp = h->fp; ua.xf16 = h->xf16; ua.xfb = h->xfb;
 
     // choice_info of the initial pheromone
     UpdateArgs refresh = ua;

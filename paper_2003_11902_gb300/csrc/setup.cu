@@ -65,8 +65,9 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 }
 
 // Candidate lists (Sec. 4.3): the cl nearest other nodes of each row in
-// ascending (distance, id) order.  One warp per row; cl rounds, each taking the
-// smallest key (d << 32 | j) above the previous round's key.
+// ascending (distance, id) order, as 32-bit and/or 16-bit ids (either output
+// may be null).  One warp per row; cl rounds, each taking the smallest key
+// (d << 32 | j) above the previous round's key.
 __global__ void k_candidates(const int32_t *__restrict__ d, int32_t n, int32_t ld, int32_t cl,
                              int32_t *__restrict__ cand32, uint16_t *__restrict__ cand16)
 {
@@ -85,7 +86,7 @@ __global__ void k_candidates(const int32_t *__restrict__ d, int32_t n, int32_t l
             }
             best = warp_min_u64(best);
             if (lane == 0) {
-                cand32[(size_t)i * cl + r] = (int32_t)(best & 0xFFFFFFFFull);
+                if (cand32) cand32[(size_t)i * cl + r] = (int32_t)(best & 0xFFFFFFFFull);
                 if (cand16) cand16[(size_t)i * cl + r] = (uint16_t)(best & 0xFFFFull);
             }
             last = best;
