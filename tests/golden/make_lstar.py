@@ -13,13 +13,20 @@ measurement.  Calls only the oracle.  Workloads:
   clustered-n3800 synthetic clustered n = 3800 (seed 1003), m = 1000, cl = 16,
                   2-opt of each iteration's best (Sec. 5.7), 500 iterations
                   -> lstar_clustered_n3800.json
+  uniform-n5000-cl16-2opt  synthetic uniform n = 5000 (coordinate seed 1005),
+                  m = 5000, cl = 16, 2-opt of each iteration's best; the plain
+                  colony of the learned-prior race at n = 5000.  An oracle
+                  iteration there takes tens of seconds on 8 cores, so the
+                  default is MMAS seed 1 alone for 200 iterations (stated in
+                  the file) -> lstar_uniform_n5000_cl16_2opt.json
   batched-sample16 the first 16 instances with n <= 400 of the batched workload
                   (256 uniform instances, n = round(exp(U[ln 100, ln 2000])) with
                   size seed 1000, coordinate seed 1000 + index), m = n, cl = 32,
                   1000 iterations each -> lstar_batched_sample16.json (one L*
                   per instance; runs go to a pool of single-threaded processes)
 
-    python tests/golden/make_lstar.py [--workload uniform-n1000] [--iters N] [--threads N]
+    python tests/golden/make_lstar.py [--workload uniform-n1000] [--iters N] [--seeds 1,2,3]
+                                      [--threads N]
 """
 import argparse
 import json
@@ -50,6 +57,10 @@ WORKLOADS = {
                             out="lstar_clustered_n3800.json",
                             text="clustered n=3800 (seed 1003), m=1000, cl=16, 2-opt of the iteration "
                                  "best, alpha=1, beta=2, rho=0.02, p_best=0.01"),
+    "uniform-n5000-cl16-2opt": dict(kind="uniform", n=5000, iseed=1005, m=5000, cl=16, ls=1, iters=200,
+                                    seeds=(1,), out="lstar_uniform_n5000_cl16_2opt.json",
+                                    text="uniform n=5000 (coordinate seed 1005), m=5000, cl=16, 2-opt of the "
+                                         "iteration best, alpha=1, beta=2, rho=0.02, p_best=0.01"),
 }
 
 
@@ -104,6 +115,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-sample16"], default="uniform-n1000")
     ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--seeds", type=str, default=None, help="comma-separated MMAS seeds")
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     args = ap.parse_args()
     if args.workload == "batched-sample16":
@@ -111,8 +123,9 @@ def main():
     w = WORKLOADS[args.workload]
     iters = args.iters or w["iters"]
     xy = instance(w)
+    seeds = tuple(int(x) for x in args.seeds.split(",")) if args.seeds else w.get("seeds", (1, 2, 3))
     runs = []
-    for seed in (1, 2, 3):
+    for seed in seeds:
         t0 = time.time()
         col = O.Colony(xy=xy, m=w["m"], cl=w["cl"], alpha=1.0, beta=2.0, rho=float(np.float32(0.02)),
                        p_best=float(np.float32(0.01)), seed=seed, ls=w["ls"])
@@ -123,7 +136,7 @@ def main():
         runs.append({"seed": seed, "best": trace[-1], "trace_every_50": trace[49::50],
                      "seconds": round(time.time() - t0, 1)})
         print(seed, trace[-1], runs[-1]["seconds"], flush=True)
-    out = {"workload": w["text"], "iterations": iters,
+    out = {"workload": w["text"], "iterations": iters, "seeds": list(seeds),
            "lstar": min(r["best"] for r in runs), "runs": runs,
            "source": "tests/golden/make_lstar.py (CPU oracle)"}
     with open(os.path.join(HERE, w["out"]), "w") as f:
