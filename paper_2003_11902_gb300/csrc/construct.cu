@@ -365,8 +365,7 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
                                           int lane, int mode, uint32_t t, uint32_t ant, uint32_t it,
                                           uint32_t k0, uint32_t k1, uint32_t *err, int cur,
                                           const uint2 *xl, const float *xb, const uint2 *xx,
-                                          const int32_t *xn, int xe, const uint16_t *xf, int fe,
-                                          const float *xfb)
+                                          const int32_t *xn, int xe, const FarList *far)
 {
     const bool sparse = TW == 0 && n - (int)t <= SPARSE_SCAN_MAX;  // few nodes left: read only those
     if (mode == 0) {
@@ -374,8 +373,10 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
             uint32_t mx, v;
             const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane, mx, v);
             if (r >= 0) return r;
-            if (fe > 0 && !sparse) {
-                const int r2 = greedy_far<TW>(row, xf, xfb, tb, lane, mx, v);
+            if (far && !sparse) {
+                const FarList f = *far;
+                const int r2 = greedy_far<TW>(row, f.xf16 + (size_t)cur * f.fp + REACH_MAX, f.xfb + cur, tb,
+                                              lane, mx, v);
                 if (r2 >= 0) return r2;
             }
         }
@@ -431,8 +432,7 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
                                             (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
                                             cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
-                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
                           fbn);
 }
 
@@ -536,8 +536,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
             cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                               (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                               a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
-                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
+                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
             fbn);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
@@ -808,8 +807,7 @@ __device__ __forceinline__ int cand_step2(const ConstructArgs &a, const Tabu<TW>
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                                             (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                                             a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe,
-                                            a.xf16 + (size_t)cur * a.fp + REACH_MAX, a.fe, a.xfb + cur),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
                           fbn);
 }
 

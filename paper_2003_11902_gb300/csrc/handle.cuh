@@ -40,6 +40,7 @@ struct mmas_handle {
     int32_t fe = 0, fp = 0;          // far list of the greedy fallback: entries past the reach list, row pitch
     uint16_t *xf16 = nullptr;        // [n][fp]
     float *xfb = nullptr;            // [n]
+    mmas::FarList *far = nullptr;    // device copy of {xf16, xfb, fp} for the construction
     mmas::Scalars *h_sc = nullptr;  // pinned mirror of *sc
     int32_t *h_tour = nullptr;      // pinned staging of the best tour
 

@@ -216,14 +216,21 @@ struct ConstructArgs {
     const float *xlb;          // [n]
     const uint2 *xxw;          // [n][REACH_EXTRA] nodes outside the list above the trail floor
     const int32_t *xxn;        // [n] how many of them are stored
-    // far list (rows of n >= REACH_FAR_MIN_N; fe = 0: none, else fe = REACH_FAR -
-    // REACH_MAX): per row the nodes ranked REACH_MAX + 1 .. REACH_FAR by
-    // (distance, id), at entries REACH_MAX .. of a row of xf16 (pitch fp =
-    // REACH_FAR; the first REACH_MAX entries repeat the reach list), and a
-    // bound on the choice_info of every node beyond them
-    int32_t fe, fp;
-    const uint16_t *xf16;      // [n][fp]
-    const float *xfb;          // [n]
+    // far list (rows of n >= REACH_FAR_MIN_N), in device memory, or nullptr:
+    // none.  Behind one pointer so the steps' fallback calls stay as light as
+    // without it
+    const struct FarList *far;
+};
+
+// Far list of a colony's greedy fallback: per row the nodes ranked REACH_MAX +
+// 1 .. REACH_FAR by (distance, id), at entries REACH_MAX .. of a row of xf16
+// (pitch fp = REACH_FAR; the first REACH_MAX entries repeat the reach list),
+// and a bound on the choice_info of every node beyond them.
+struct FarList {
+    const uint16_t *xf16;  // [n][fp]
+    const float *xfb;      // [n]
+    int32_t fp;
+    int32_t pad;
 };
 
 // Longest reach list of the greedy fallback (lane l of a warp holds entries
@@ -238,10 +245,14 @@ constexpr int REACH_EXTRA = 32;
 // choice_info is gathered from the row and compared with a bound on the rest,
 // which replaces most row scans (uniform n = 18,500: 88% of the fallbacks are
 // decided by the 128 nearest, 98.7% by the 1024 nearest).  Shorter rows scan
-// in few round trips, and there the list's upkeep cost more than it saved
-// (n = 5,000: 6.29 ms of construction with it, 6.14 without).
+// in few round trips, and there the list cost more than it saved (n = 5,000:
+// 6.29 ms of construction with it, 6.14 without).
 constexpr int REACH_FAR = 1024;
-constexpr int REACH_FAR_MIN_N = 8192;
+// The fused pass gives each row a CTA up to this many rows, else a warp.
+constexpr int UPDATE_CTA_MAX_N = 8192;
+// Far lists only for colonies whose rows the warp form updates (it computes
+// their bound; the CTA form, used for fewer rows, has no far-list code).
+constexpr int REACH_FAR_MIN_N = UPDATE_CTA_MAX_N + 1;
 static_assert((REACH_FAR - REACH_MAX) % 64 == 0 && REACH_FAR_MIN_N > REACH_FAR,
               "far-list entries come two to a word, 32 words a warp round; rows hold REACH_FAR nodes");
 

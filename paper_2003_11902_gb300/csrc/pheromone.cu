@@ -197,14 +197,9 @@ template <bool FULLROW, bool ALPHA1, bool EXTRAS>
 __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float tmin, float tmax,
                                                float delta)
 {
-    __shared__ uint32_t s_bound[8], s_ball[8], s_bfar[8];
+    __shared__ uint32_t s_bound[8], s_ball[8];
     __shared__ int s_nx, s_hot[8];
-    const bool reach = !FULLROW && a.xe > 0;
-    // far list: the bound covers every node j != i with eta^beta_ij at most that
-    // of the row's last far node (every node beyond the list)
-    const bool far = reach && a.fe > 0;
-    const float thr_far = far ? __ldg(a.eb + (size_t)i * a.ld + a.xf16[(size_t)i * a.fp + a.fp - 1]) : -1.0f;
-    float bound_far = 0.0f;
+    const bool reach = !FULLROW && a.xe > 0;  // (no far list: n <= UPDATE_CTA_MAX_N)
     // the extra list (xhot set) is filled only for rows that had few nodes
     // above the trail floor outside the list at the last pass (that changes
     // slowly); the others just count theirs
@@ -271,7 +266,6 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
                 }
                 if (!stored) bound = fmaxf(bound, w);
                 if (EXTRAS) bound_all = fmaxf(bound_all, w);
-                if (far && ev[c] <= thr_far) bound_far = fmaxf(bound_far, w);
             }
         }
         trow[q] = make_float4(tv[0], tv[1], tv[2], tv[3]);
@@ -281,10 +275,6 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
         if (reach) {  // choice_info >= 0: its bits order like the values
             const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound));
             if ((threadIdx.x & 31) == 0) s_bound[threadIdx.x >> 5] = wmax;
-            if (far) {
-                const uint32_t fmax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_far));
-                if ((threadIdx.x & 31) == 0) s_bfar[threadIdx.x >> 5] = fmax;
-            }
             if (extras) {
                 const uint32_t amax = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(bound_all));
                 const int hots = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)hot_cnt);
@@ -322,11 +312,6 @@ __device__ __forceinline__ void update_row_cta(const UpdateArgs &a, int i, float
                 a.xlb[i] = __uint_as_float(all || !extras ? m : ma);
                 a.xxn[i] = all ? hots : 0;
                 if (extras) a.xhot[i] = hots;
-                if (far) {
-                    uint32_t mf = 0;
-                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mf = s_bfar[w] > mf ? s_bfar[w] : mf;
-                    a.xfb[i] = __uint_as_float(mf);
-                }
             }
             __syncthreads();  // s_bound is read before the CTA's next row writes it
         }
@@ -538,7 +523,7 @@ cudaError_t launch_update_batch(const UpdateArgs *args, const int32_t *row_colon
 cudaError_t launch_update(const UpdateArgs &a, int num_sms, cudaStream_t s)
 {
     const bool a1 = a.alpha == 1.0f;
-    if (a.n <= 8192) {  // a CTA per row: few rows, each one's latency counts
+    if (a.n <= UPDATE_CTA_MAX_N) {  // a CTA per row: few rows, each one's latency counts
         const int grid = a.n < num_sms * 8 ? a.n : num_sms * 8;
         if (a.fullrow) {
             if (a1) k_update_cta<true, true><<<grid, 256, 0, s>>>(a);

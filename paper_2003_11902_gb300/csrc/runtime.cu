@@ -74,7 +74,7 @@ void free_all(mmas_handle *h)
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
                     h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->ext_bad, h->nnd,
                     h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot,
-                    h->xf16,    h->xfb};
+                    h->xf16,    h->xfb,    h->far};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -307,6 +307,10 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
             CK(h, dalloc(&h->xf16, (size_t)n * h->fp * sizeof(uint16_t), h->stream));
             CK(h, dalloc(&h->xfb, (size_t)n * sizeof(float), h->stream));
             CK(h, launch_candidates(h->dist, n, ld, h->fp, nullptr, h->xf16, s));
+            CK(h, dalloc(&h->far, sizeof(FarList), h->stream));
+            const FarList fl{h->xf16, h->xfb, h->fp, 0};
+            CK(h, cudaMemcpyAsync(h->far, &fl, sizeof(fl), cudaMemcpyHostToDevice, s));
+            CK(h, cudaStreamSynchronize(s));  // fl is on the host stack
         }
     }
     CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, s));
@@ -328,7 +332,7 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     ca.cand16 = h->cand16; ca.cwinv = h->cwinv; ca.wmat = h->wmat;
     ca.tours = h->tours; ca.sc = h->sc;
     ca.xe = h->xe; ca.xlw = h->xlw; ca.xlb = h->xlb; ca.xxw = h->xxw; ca.xxn = h->xxn;
-    ca.fe = h->fe; ca.fp = h->fp; ca.xf16 = h->xf16; ca.xfb = h->xfb;
+    ca.far = h->far;
     ca.stage_w_bytes = (uint32_t)cw_bytes;
     ca.stage_c_bytes = (uint32_t)cc_bytes;
     if (cl == 0) { ca.stage_w_bytes = 0; ca.stage_c_bytes = 0; }
