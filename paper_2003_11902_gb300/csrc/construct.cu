@@ -373,7 +373,7 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
             uint32_t mx, v;
             const int r = greedy_reach<TW>(xl, xb, xe, xx, xn, tb, lane, mx, v);
             if (r >= 0) return r;
-            if (far && !sparse) {
+            if (TW == 0 && far && !sparse) {
                 const FarList f = *far;
                 const int r2 = greedy_far<TW>(row, f.xf16 + (size_t)cur * f.fp + REACH_MAX, f.xfb + cur, tb,
                                               lane, mx, v);
@@ -386,6 +386,18 @@ __device__ __noinline__ int cand_fallback(const float *__restrict__ row, int n, 
     if (sparse) return scan_unvisited<false>(row, n, tb.w, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
     return scan_row<TW, false, false>(row, n, tb, lane, t, ant, it, k0, k1, err, cur) | FB_SCANNED;
 }
+
+// The far list reaches the fallback only from kernels whose tabus live in
+// shared memory (TW = 0): far lists exist for n > REACH_FAR_MIN_N > 4096 only,
+// and register-tabu kernels pass a constant null (their step loop stays as
+// without it).
+template <int TW>
+__device__ __forceinline__ const FarList *far_of(const ConstructArgs &a)
+{
+    if constexpr (TW == 0) return a.far;
+    else return nullptr;
+}
+static_assert(REACH_FAR_MIN_N > 4096, "register tabus (n <= 4096) never see a far list");
 
 // Count one fallback step in fbn's low half and, when its row was scanned
 // (FB_SCANNED set in the fallback's result), one row scan in its high half;
@@ -432,7 +444,7 @@ __device__ __forceinline__ int cand_step(const ConstructArgs &a, const uint16_t 
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback,
                                             (uint32_t)t, (uint32_t)ant, it, a.key0, a.key1, &a.sc->err,
                                             cur, a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, far_of<TW>(a)),
                           fbn);
 }
 
@@ -536,7 +548,7 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
             cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                               (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                               a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
+                              a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, far_of<TW>(a)),
             fbn);
         tb.mark(lane, fb);
         twin = (lane == tb32 + jfail) ? fb : twin;
@@ -807,7 +819,7 @@ __device__ __forceinline__ int cand_step2(const ConstructArgs &a, const Tabu<TW>
     return count_fallback(cand_fallback<TW>(a.wmat + (size_t)cur * a.ld, a.n, tb, lane, a.fallback, (uint32_t)t,
                                             (uint32_t)ant, it, a.key0, a.key1, &a.sc->err, cur,
                                             a.xlw + (size_t)cur * a.xe, a.xlb + cur,
-                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, a.far),
+                                            a.xxw + (size_t)cur * REACH_EXTRA, a.xxn + cur, a.xe, far_of<TW>(a)),
                           fbn);
 }
 
