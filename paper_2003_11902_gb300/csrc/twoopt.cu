@@ -161,32 +161,37 @@ __device__ __forceinline__ bool nint_sqrt_below(long long s, long long t)
     return t > 0 && s <= t * t - t;
 }
 
-// First improving move at city c1, searched by one warp: lane h examines
-// neighbour h (h < k <= 32) on both sides.  The sequential scan of a side stops
-// at the first neighbour not closer than the tour neighbour on that side; the
-// lists are sorted by distance, so the neighbours it examines are exactly those
-// with d(c1, c2) below that radius, and its first improving one is the lowest
-// such lane whose gain is positive.  The successor side wins over the
-// predecessor side.  Every lane returns the same result.
+// First improving move at city c1, searched by one warp (PAIR: by one half of
+// a warp, lanes 16 half .. 16 half + 15, each half with its own city; k <= 16):
+// lane h examines neighbour h (h < k) on both sides.  The sequential scan of a
+// side stops at the first neighbour not closer than the tour neighbour on that
+// side; the lists are sorted by distance, so the neighbours it examines are
+// exactly those with d(c1, c2) below that radius, and its first improving one
+// is the lowest such lane whose gain is positive.  The successor side wins
+// over the predecessor side.  Every lane of the warp (the half) returns the
+// same result; act = false: a half with nothing to search (c1 must still be a
+// city), which finds nothing.  Every lane of the warp calls it.
 // fp (when not null) receives the footprint's positions: p = pos[c1] in
 // fp[0], and pos of neighbour h in fp[1 + h].
-template <bool XY, bool STAGED>
+template <bool XY, bool STAGED, bool PAIR>
 __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geometry<XY, STAGED> &g,
-                                               const TourView &tv, int c1, int lane, Move &mv,
-                                               uint16_t *fp)
+                                               const TourView &tv, int c1, int lane, bool act,
+                                               Move &mv, uint16_t *fp)
 {
+    const int hl = PAIR ? (lane & 15) : lane;  // lane within the searching group
+    const int sh = PAIR ? (lane & 16) : 0;     // the group's first lane
     const int p = tv.pos[c1];
-    if (fp && lane == 0) fp[0] = (uint16_t)p;
+    if (fp && hl == 0) fp[0] = (uint16_t)p;
     const int pn = tv.nxt(p), pp = tv.prv(p);
     const int s1 = tv.tour[pn], p1 = tv.tour[pp];
     const int rs = tv.edge[p], rp = tv.edge[pp];
     bool vs = false, vp = false;
     int q = 0, d12 = 0, tn = 0, tp = 0, dss = 0, dpp = 0;
-    if (lane < a.k) {
-        const int c2 = g.neighbour(c1, lane);
-        d12 = g.neighbour_dist(c1, lane, c2);
+    if (act && hl < a.k) {
+        const int c2 = g.neighbour(c1, hl);
+        d12 = g.neighbour_dist(c1, hl, c2);
         q = tv.pos[c2];
-        if (fp) fp[1 + lane] = (uint16_t)q;
+        if (fp) fp[1 + hl] = (uint16_t)q;
         const int qn = tv.nxt(q), qp = tv.prv(q);
         tn = tv.tour[qn];
         tp = tv.tour[qp];
@@ -204,22 +209,27 @@ __device__ __forceinline__ bool find_move_warp(const TwoOptArgs &a, const Geomet
             vp = d12 < rp && dpp < tq;
         }
     }
-    const unsigned ms = __ballot_sync(0xFFFFFFFFu, vs), mp = __ballot_sync(0xFFFFFFFFu, vp);
-    if ((ms | mp) == 0u) return false;
-    const int h = __ffs(ms ? ms : mp) - 1;
+    unsigned ms = __ballot_sync(0xFFFFFFFFu, vs), mp = __ballot_sync(0xFFFFFFFFu, vp);
+    if constexpr (PAIR) {
+        ms = (ms >> sh) & 0xFFFFu;
+        mp = (mp >> sh) & 0xFFFFu;
+    } else {
+        if ((ms | mp) == 0u) return false;  // the same in every lane
+    }
+    const bool found = (ms | mp) != 0u;
+    const int h = found ? __ffs(ms ? ms : mp) - 1 : 0;
     int d34 = ms ? dss : dpp;
     if constexpr (XY) {
-        if (lane == h) d34 = ms ? g.d(s1, tn) : g.d(p1, tp);  // the added edge, exactly
+        if (found && hl == h) d34 = ms ? g.d(s1, tn) : g.d(p1, tp);  // the added edge, exactly
     }
     mv.c1 = c1;
     mv.side = ms ? 0 : 1;
     mv.p = p;
-    mv.q = __shfl_sync(0xFFFFFFFFu, q, h);
-    mv.d12 = __shfl_sync(0xFFFFFFFFu, d12, h);
-    mv.d34 = __shfl_sync(0xFFFFFFFFu, d34, h);
-    return true;
+    mv.q = __shfl_sync(0xFFFFFFFFu, q, sh + h);
+    mv.d12 = __shfl_sync(0xFFFFFFFFu, d12, sh + h);
+    mv.d34 = __shfl_sync(0xFFFFFFFFu, d34, sh + h);
+    return found;
 }
-
 
 // Reverse tour[pa..pb] (len cities, cyclic) with `count` threads numbered
 // `t`; the len - 1 edges inside the path reverse with it.
@@ -374,16 +384,17 @@ __device__ __forceinline__ uint32_t keep_hits(const RoundKeep &kp, const Move *s
 }
 
 // Warp 0, after the round whose lowest improving city is `first` (window
-// cities from l; cities below lim were each kept by warp c - l): apply that
+// cities from l; city c's move, if any, is in slot (c - l) mod SL; cities below
+// lim were kept in slot c - l): apply that
 // move, then walk on through first + 1 .. lim - 1 while the kept results
 // hold (no hit from a move applied so far).  Returns the next city to search
 // and sets moves.
 __device__ __forceinline__ int apply_moves(const TourView &tv, uint32_t *dlb, const Move *s_move,
-                                           const RoundKeep &kp, int l, int first, int lim, int NW,
+                                           const RoundKeep &kp, int l, int first, int lim, int SL,
                                            int lane, int &moves)
 {
     int len = 0;
-    apply_move(tv, dlb, s_move[(first - l) & (NW - 1)], l, lane, len);
+    apply_move(tv, dlb, s_move[(first - l) & (SL - 1)], l, lane, len);
     if (first >= lim) {
         moves = 1;
         return first + 1;
@@ -410,14 +421,23 @@ __device__ __forceinline__ int apply_moves(const TourView &tv, uint32_t *dlb, co
     return c;
 }
 
-template <bool XY, bool STAGED, bool IB>
+// PAIR: k <= 16 and at most 16 warps; each warp searches two cities at a time
+// (a half each), so a window's first 16 cities take 8 warps.
+template <bool XY, bool STAGED, bool IB, bool PAIR>
 __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n, tid = threadIdx.x, W = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, NW = W >> 5;
-    // cities in the first window after a move: one a warp, as far as results are kept
-    const int first_window = NW < MM_MAX ? NW : MM_MAX;
+    // cities searched at a time: one a warp, two with PAIR; city c of a window
+    // from l is searched in slot (c - l) mod SL (its move slot), by warp
+    // slot / S and, with PAIR, its half slot % 2
+    constexpr int S = PAIR ? 2 : 1;
+    const int SL = S * NW;
+    const int slot0 = S * warp + (PAIR ? (lane >> 4) : 0);
+    const int gl = PAIR ? (lane & 15) : lane;  // lane within the searching group
+    // cities in the first window after a move: one a slot, as far as results are kept
+    const int first_window = SL < MM_MAX ? SL : MM_MAX;
     const Layout L = Layout::make(n, a.k, STAGED);
     TourView tv;
     tv.n = n;
@@ -431,7 +451,7 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
     __shared__ int s_first[3];
     __shared__ Move s_move[32];  // per warp
     __shared__ RoundKeep s_keep;
-    const int mm = NW < MM_MAX ? NW : MM_MAX;  // window cities whose results are kept
+    const int mm = SL < MM_MAX ? SL : MM_MAX;  // window cities whose results are kept
     __shared__ int s_red[32];
     __shared__ unsigned long long s_best;
 
@@ -492,27 +512,34 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                 while (l < n) {  // windows
                     const int wend = l + w < n ? l + w : n;
                     int mine = INT_MAX;
-                    for (int c1 = l + warp; c1 < wend; c1 += NW) {  // warp-uniform
-                        const bool keep = c1 == l + warp && warp < mm;
-                        if (dlb_get(s_dlb, c1)) {
-                            if (keep && lane == 0) {
-                                s_keep.res[warp] = 0;
-                                s_keep.fp[warp][0] = (uint16_t)tv.pos[c1];
-                            }
-                            continue;
+                    // this group's cities l + slot0, l + slot0 + SL, ... up to its
+                    // first move; the loop runs while either half of the warp has one
+                    int c1 = l + slot0;
+                    bool live = c1 < wend;
+                    bool first_city = true;
+                    while (__any_sync(0xFFFFFFFFu, live)) {  // warp-uniform
+                        const bool keep = live && first_city && slot0 < mm;
+                        const bool skip = live && dlb_get(s_dlb, c1);
+                        if (keep && skip && gl == 0) {
+                            s_keep.res[slot0] = 0;
+                            s_keep.fp[slot0][0] = (uint16_t)tv.pos[c1];
                         }
+                        const bool act = live && !skip;
                         Move mv;
-                        const bool found = find_move_warp<XY, STAGED>(a, g, tv, c1, lane, mv,
-                                                                      keep ? s_keep.fp[warp] : nullptr);
-                        if (keep && lane == 0) s_keep.res[warp] = found ? 2 : 1;
-                        if (found) {
-                            if (lane == 0) s_move[warp] = mv;
+                        const bool found = find_move_warp<XY, STAGED, PAIR>(
+                            a, g, tv, act ? c1 : 0, lane, act, mv, (keep && act) ? s_keep.fp[slot0] : nullptr);
+                        if (keep && act && gl == 0) s_keep.res[slot0] = found ? 2 : 1;
+                        if (found) {  // (act, since nothing is found otherwise)
+                            if (gl == 0) s_move[slot0] = mv;
                             mine = c1;
-                            break;
+                            live = false;
                         }
+                        c1 += SL;
+                        live = live && c1 < wend;
+                        first_city = false;
                     }
                     int *slot = s_first + round % 3;
-                    if (lane == 0 && mine != INT_MAX) atomicMin(slot, mine);
+                    if (gl == 0 && mine != INT_MAX) atomicMin(slot, mine);
                     __syncthreads();
                     const int first = *slot;
                     if (tid == 0) s_first[(round + 2) % 3] = INT_MAX;  // no one reads it for two rounds
@@ -523,21 +550,22 @@ __global__ void __launch_bounds__(1024, 1) k_two_opt(const TwoOptArgs a)
                         w = w * 2 < W ? w * 2 : W;
                         continue;
                     }
-                    // cities [l, first) were evaluated without a move (every warp
+                    // cities [l, first) were evaluated without a move (every group
                     // stopped at its own first move, so all of them were reached);
-                    // city c was searched by warp (c - l) mod NW
+                    // city c was searched in slot (c - l) mod SL
                     const int lim = wend < l + mm ? wend : l + mm;
-                    if (first < lim) {  // the kept cities after first: hits, one warp each
-                        const int j = warp;
-                        if (l + j > first && l + j < lim) {
-                            const uint32_t h = keep_hits(s_keep, s_move, j, a.k, n, lane);
-                            if (lane == 0) s_keep.hit[j] = h;
+                    if (first < lim) {  // the kept cities after first: hits, a warp each
+                        for (int j = warp; j < mm; j += NW) {
+                            if (l + j > first && l + j < lim) {
+                                const uint32_t h = keep_hits(s_keep, s_move, j, a.k, n, lane);
+                                if (lane == 0) s_keep.hit[j] = h;
+                            }
                         }
                         __syncthreads();
                     }
                     if (warp == 0) {
                         int moves = 0;
-                        const int next = apply_moves(tv, s_dlb, s_move, s_keep, l, first, lim, NW,
+                        const int next = apply_moves(tv, s_dlb, s_move, s_keep, l, first, lim, SL,
                                                      lane, moves);
                         if (lane == 0) {
                             s_keep.next = next;
@@ -591,14 +619,23 @@ __global__ void k_neighbour_dist(const TwoOptArgs a, int32_t *nnd)
     }
 }
 
+template <bool XY, bool STAGED, bool IB, bool PAIR>
+cudaError_t launch_pair(const TwoOptArgs &a, int grid, int threads, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_two_opt<XY, STAGED, IB, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_two_opt<XY, STAGED, IB, PAIR><<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Two cities a warp when the lists are at most 16 long and the slots (two a
+// warp) fit the 32 move slots.
 template <bool XY, bool STAGED, bool IB>
 cudaError_t launch_one(const TwoOptArgs &a, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_two_opt<XY, STAGED, IB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_two_opt<XY, STAGED, IB><<<grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.k <= 16 && threads <= 512) return launch_pair<XY, STAGED, IB, true>(a, grid, threads, smem, s);
+    return launch_pair<XY, STAGED, IB, false>(a, grid, threads, smem, s);
 }
 
 }  // namespace
