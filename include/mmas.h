@@ -145,8 +145,10 @@ typedef struct {
     int32_t construct_staged;  /* 1 if the choice table is staged in shared memory   */
     int32_t construct_smem;    /* dynamic shared memory per CTA, bytes               */
     int32_t row_pitch;         /* elements per row of the n x n device matrices      */
-    int64_t fallback_scans;    /* of the fallback steps, those that scanned the whole
-                                  row (the rest were decided on the reach list)      */
+    int64_t fallback_scans;    /* of the fallback steps, those that scanned the row
+                                  (the rest were decided on the nearest nodes' lists:
+                                  the 128 nearest, and above 8,192 nodes the 1024
+                                  nearest)                                          */
 } mmas_stats_t;
 
 /* Fill *p with the defaults listed at mmas_params (m = 0 means "m = n"). */
