@@ -346,8 +346,8 @@ cudaError_t launch_eta_beta(const int32_t *d, int32_t n, int32_t ld, double beta
                             cudaStream_t s);
 cudaError_t launch_candidates(const int32_t *d, int32_t n, int32_t ld, int32_t cl,
                               int32_t *cand32, uint16_t *cand16, cudaStream_t s);
-cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour,
-                           Scalars *sc, cudaStream_t s);
+cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour, Scalars *sc,
+                           const void *list, bool list16, int L, int P, cudaStream_t s);
 cudaError_t launch_init_colony(int32_t n, int32_t ld, double rho, double p_root, float *tau,
                                Scalars *sc, cudaStream_t s);
 

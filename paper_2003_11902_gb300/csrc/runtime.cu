@@ -313,7 +313,13 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
             CK(h, cudaStreamSynchronize(s));  // fl is on the host stack
         }
     }
-    CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, s));
+    // the nearest-neighbour tour reads the longest sorted list there is
+    if (h->xf16)
+        CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, h->xf16, true, h->fp, h->fp, s));
+    else if (h->xl32)
+        CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, h->xl32, false, h->xe, h->xe, s));
+    else
+        CK(h, launch_nn_tour(h->dist, n, ld, h->nn_tour, h->sc, cl > 0 ? h->cand32 : nullptr, false, cl, cl, s));
     CK(h, launch_init_colony(n, ld, (double)h->p.rho, h->p_root, h->tau, h->sc, s));
 
     // launch arguments of one iteration

@@ -95,10 +95,16 @@ __global__ void k_candidates(const int32_t *__restrict__ d, int32_t n, int32_t l
 }
 
 // Nearest-neighbour tour from node 0, ties -> lower id (one CTA, n sequential
-// arg-min steps over the current row), and its length into sc->nn_len.
+// arg-min steps), and its length into sc->nn_len.  With a list of each row's
+// nearest nodes in (distance, id) order (list: L entries a row, pitch P, 16-
+// or 32-bit ids; L = 0: none), a step takes the first unvisited entry of the
+// current row's list -- every node outside the list comes after all of its
+// entries in that order -- and scans the row only when the whole list is
+// visited.
+template <typename T>
 __global__ void __launch_bounds__(1024) k_nn_tour(const int32_t *__restrict__ d, int32_t n,
                                                   int32_t ld, int32_t *__restrict__ tour,
-                                                  Scalars *sc)
+                                                  Scalars *sc, const T *__restrict__ list, int L, int P)
 {
     extern __shared__ unsigned char vis[];
     __shared__ unsigned long long red[32];
@@ -111,36 +117,73 @@ __global__ void __launch_bounds__(1024) k_nn_tour(const int32_t *__restrict__ d,
     }
     __syncthreads();
     int cur = 0;
-    long long len = 0;
     for (int t = 1; t < n; ++t) {
-        const int32_t *row = d + (size_t)cur * ld;
-        unsigned long long best = ~0ull;
-        for (int j = tid; j < n; j += blockDim.x)
-            if (!vis[j]) {
-                const unsigned long long key =
-                    ((unsigned long long)(uint32_t)row[j] << 32) | (uint32_t)j;
-                best = key < best ? key : best;
+        unsigned long long b = ~0ull;
+        if (L > 0) {  // the first unvisited entry of cur's list (the same in every thread)
+            const T *lrow = list + (size_t)cur * P;
+            unsigned long long e_best = ~0ull;
+            for (int e = tid; e < L; e += blockDim.x) {
+                const int v = (int)lrow[e];
+                if (!vis[v]) {
+                    const unsigned long long key = ((unsigned long long)(uint32_t)e << 32) | (uint32_t)v;
+                    e_best = key < e_best ? key : e_best;
+                }
             }
-        best = warp_min_u64(best);
-        if (lane == 0) red[warp] = best;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long v = lane < nwarps ? red[lane] : ~0ull;
-            v = warp_min_u64(v);
-            if (lane == 0) red[0] = v;
+            e_best = warp_min_u64(e_best);
+            if (lane == 0) red[warp] = e_best;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long v = lane < nwarps ? red[lane] : ~0ull;
+                v = warp_min_u64(v);
+                if (lane == 0) red[0] = v;
+            }
+            __syncthreads();
+            b = red[0];
+            __syncthreads();  // red is read before it is written again
         }
-        __syncthreads();
-        const unsigned long long b = red[0];
+        if (b == ~0ull) {  // no list, or every listed node visited: scan the row
+            const int32_t *row = d + (size_t)cur * ld;
+            unsigned long long best = ~0ull;
+            for (int j = tid; j < n; j += blockDim.x)
+                if (!vis[j]) {
+                    const unsigned long long key =
+                        ((unsigned long long)(uint32_t)row[j] << 32) | (uint32_t)j;
+                    best = key < best ? key : best;
+                }
+            best = warp_min_u64(best);
+            if (lane == 0) red[warp] = best;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned long long v = lane < nwarps ? red[lane] : ~0ull;
+                v = warp_min_u64(v);
+                if (lane == 0) red[0] = v;
+            }
+            __syncthreads();
+            b = red[0];
+        }
         const int nxt = (int)(b & 0xFFFFFFFFull);
         if (tid == 0) {
             vis[nxt] = 1;
             tour[t] = nxt;
-            len += (long long)(b >> 32);
         }
         cur = nxt;
         __syncthreads();
     }
-    if (tid == 0) sc->nn_len = len + d[(size_t)cur * ld + 0];
+    // the length, from the finished tour (written by thread 0, visible after
+    // the barrier)
+    long long part = 0;
+    for (int t = tid; t < n; t += blockDim.x) {
+        const int u = tour[t], v = tour[t + 1 < n ? t + 1 : 0];
+        part += d[(size_t)u * ld + v];
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+    if (lane == 0) red[warp] = (unsigned long long)part;
+    __syncthreads();
+    if (tid == 0) {
+        long long len = 0;
+        for (int w = 0; w < nwarps; ++w) len += (long long)red[w];
+        sc->nn_len = len;
+    }
 }
 
 // Initial limits from the nearest-neighbour length, scalars reset, and
@@ -202,13 +245,22 @@ cudaError_t launch_candidates(const int32_t *d, int32_t n, int32_t ld, int32_t c
     return cudaGetLastError();
 }
 
-cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour,
-                           Scalars *sc, cudaStream_t s)
+cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour, Scalars *sc,
+                           const void *list, bool list16, int L, int P, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_nn_tour, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         65536);
-    if (e != cudaSuccess) return e;
-    k_nn_tour<<<1, 1024, (size_t)n, s>>>(d, n, ld, tour, sc);
+    if (list16) {
+        cudaError_t e = cudaFuncSetAttribute(k_nn_tour<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             65536);
+        if (e != cudaSuccess) return e;
+        k_nn_tour<uint16_t><<<1, 1024, (size_t)n, s>>>(d, n, ld, tour, sc, static_cast<const uint16_t *>(list),
+                                                       L, P);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_nn_tour<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             65536);
+        if (e != cudaSuccess) return e;
+        k_nn_tour<int32_t><<<1, 1024, (size_t)n, s>>>(d, n, ld, tour, sc, static_cast<const int32_t *>(list),
+                                                      list ? L : 0, P);
+    }
     return cudaGetLastError();
 }
 
