@@ -66,31 +66,93 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 
 // Candidate lists (Sec. 4.3): the cl nearest other nodes of each row in
 // ascending (distance, id) order, as 32-bit and/or 16-bit ids (either output
-// may be null).  One warp per row; cl rounds, each taking the smallest key
-// (d << 32 | j) above the previous round's key.
+// may be null).  One warp per row, cl <= SELECT_MAX:
+//  1. the cl-th smallest distance T of the row (j != i): the smallest T with at
+//     least cl distances <= T, by bisection on [0, max] with one counting pass
+//     of the row per halving (about log2 max passes);
+//  2. the keys (d << 32 | j) of every node with d < T and of the lowest-id
+//     nodes with d = T, cl in all, into the warp's shared memory (chunks of 32
+//     consecutive ids in order, so the ties taken are the lowest ids);
+//  3. a bitonic sort of those keys (padded to a power of two) in shared memory.
+constexpr int SELECT_MAX = 1024;
+
+__device__ __forceinline__ int pow2_at_least(int k)
+{
+    int p = 1;
+    while (p < k) p <<= 1;
+    return p;
+}
+
 __global__ void k_candidates(const int32_t *__restrict__ d, int32_t n, int32_t ld, int32_t cl,
                              int32_t *__restrict__ cand32, uint16_t *__restrict__ cand16)
 {
+    extern __shared__ unsigned long long s_keys[];  // pow2_at_least(cl) per warp
     const int lane = threadIdx.x & 31;
+    const int kp = pow2_at_least(cl);
+    unsigned long long *keys = s_keys + (size_t)(threadIdx.x >> 5) * kp;
     const int warps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned below = (1u << lane) - 1u;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         const int32_t *row = d + (size_t)i * ld;
-        unsigned long long last = 0;
-        for (int r = 0; r < cl; ++r) {
-            unsigned long long best = ~0ull;
-            for (int j = lane; j < n; j += 32) {
-                if (j == i) continue;
-                const unsigned long long key =
-                    ((unsigned long long)(uint32_t)row[j] << 32) | (uint32_t)j;
-                if ((r == 0 || key > last) && key < best) best = key;
+        int mx = 0;
+        for (int j = lane; j < n; j += 32)
+            if (j != i) mx = row[j] > mx ? row[j] : mx;
+        mx = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)mx);
+        // 1. T: count(d <= lo) < cl <= count(d <= hi)
+        long long lo = -1, hi = mx;
+        int c_lo = 0;
+        while (hi - lo > 1) {
+            const int mid = (int)(lo + (hi - lo) / 2);
+            int c = 0;
+            for (int j = lane; j < n; j += 32) c += (j != i && row[j] <= mid) ? 1 : 0;
+            c = (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)c);
+            if (c >= cl) {
+                hi = mid;
+            } else {
+                lo = mid;
+                c_lo = c;
             }
-            best = warp_min_u64(best);
-            if (lane == 0) {
-                if (cand32) cand32[(size_t)i * cl + r] = (int32_t)(best & 0xFFFFFFFFull);
-                if (cand16) cand16[(size_t)i * cl + r] = (uint16_t)(best & 0xFFFFull);
-            }
-            last = best;
         }
+        const int T = (int)hi;
+        const int need_eq = cl - c_lo;  // nodes at distance T to take, lowest ids first
+        // 2. collect
+        int cnt = 0, eq = 0;
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            const int j = j0 + lane;
+            const int v = (j < n && j != i) ? row[j] : -1;
+            const bool lt = v >= 0 && v < T;
+            const bool te = v == T;
+            const unsigned mte = __ballot_sync(0xFFFFFFFFu, te);
+            const bool take = lt || (te && eq + __popc(mte & below) < need_eq);
+            const unsigned mt = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) keys[cnt + __popc(mt & below)] = ((unsigned long long)(uint32_t)v << 32) | (uint32_t)j;
+            cnt += __popc(mt);
+            const int te_n = __popc(mte);
+            eq += te_n < need_eq - eq ? te_n : need_eq - eq;
+        }
+        for (int e = cl + lane; e < kp; e += 32) keys[e] = ~0ull;
+        __syncwarp();
+        // 3. bitonic sort, ascending
+        for (int size = 2; size <= kp; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (kp >> 1); t += 32) {
+                    const int a = 2 * stride * (t / stride) + (t % stride), b = a + stride;
+                    const unsigned long long ka = keys[a], kb = keys[b];
+                    const bool up = (a & size) == 0;
+                    if ((ka > kb) == up) {
+                        keys[a] = kb;
+                        keys[b] = ka;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int e = lane; e < cl; e += 32) {
+            const uint32_t j = (uint32_t)(keys[e] & 0xFFFFFFFFull);
+            if (cand32) cand32[(size_t)i * cl + e] = (int32_t)j;
+            if (cand16) cand16[(size_t)i * cl + e] = (uint16_t)j;
+        }
+        __syncwarp();  // the keys are read before the warp's next row writes them
     }
 }
 
@@ -239,9 +301,16 @@ cudaError_t launch_candidates(const int32_t *d, int32_t n, int32_t ld, int32_t c
                               int32_t *cand32, uint16_t *cand16, cudaStream_t s)
 {
     if (cl <= 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = (n * 32 + threads - 1) / threads;
-    k_candidates<<<blocks, threads, 0, s>>>(d, n, ld, cl, cand32, cand16);
+    if (cl > SELECT_MAX) return cudaErrorInvalidValue;
+    int kp = 1;
+    while (kp < cl) kp <<= 1;
+    const int threads = 128;  // 4 warps, one row each at a time
+    const size_t smem = (size_t)(threads / 32) * kp * sizeof(unsigned long long);
+    cudaError_t e = cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int rows_per_wave = 152 * 8 * (threads / 32);
+    const int blocks = ((n < rows_per_wave ? n : rows_per_wave) * 32 + threads - 1) / threads;
+    k_candidates<<<blocks, threads, smem, s>>>(d, n, ld, cl, cand32, cand16);
     return cudaGetLastError();
 }
 
