@@ -27,6 +27,8 @@ struct mmas_handle {
     int2 *nbr = nullptr;
     mmas::Scalars *sc = nullptr;
     int *maxd = nullptr;
+    int32_t maxd_val = 0;            // the instance's largest distance
+    float *ebt = nullptr;            // [maxd_val + 1] eta^beta of each distance value, or null
     int32_t *ext_tour = nullptr, *ext_len = nullptr;
     uint32_t *ext_bad = nullptr;     // set when a device-side tour was refused (skip that update)
     int32_t *nnd = nullptr;

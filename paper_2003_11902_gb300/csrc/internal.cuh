@@ -342,8 +342,12 @@ inline cudaError_t device_malloc(T **p, size_t bytes)
 cudaError_t launch_distances(const int2 *xy, int32_t n, int32_t ld, int32_t *d, int *maxd,
                              cudaStream_t s);
 cudaError_t launch_max_dist(const int32_t *d, int32_t n, int32_t ld, int *maxd, cudaStream_t s);
+// eta^beta of every cell; with `table` (maxd + 1 floats, maxd >= every
+// distance) through a table of the distance values, else cell by cell.
 cudaError_t launch_eta_beta(const int32_t *d, int32_t n, int32_t ld, double beta, float *eb,
-                            cudaStream_t s);
+                            float *table, int32_t maxd, cudaStream_t s);
+// Largest distance for which eta^beta goes through a table (16 MB).
+constexpr int32_t ETA_TABLE_MAX = 1 << 22;
 cudaError_t launch_candidates(const int32_t *d, int32_t n, int32_t ld, int32_t cl,
                               int32_t *cand32, uint16_t *cand16, cudaStream_t s);
 cudaError_t launch_nn_tour(const int32_t *d, int32_t n, int32_t ld, int32_t *tour, Scalars *sc,

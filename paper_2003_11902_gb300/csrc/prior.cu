@@ -689,7 +689,7 @@ mmas_status mmas_prior_apply(mmas_prior *p, mmas_handle *h)
     if (st != MMAS_OK) return st;
     if ((st = forward(p, h)) != MMAS_OK) return st;
     cudaStream_t s = h->stream;
-    PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, s));
+    PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, h->ebt, h->maxd_val, s));
     k_prior_apply<<<std::min(h->n, 4096), 256, 0, s>>>(p->s, p->nn, h->n, h->ld, h->eb);
     PCK(p, cudaGetLastError());
     UpdateArgs refresh = h->uargs;
@@ -707,7 +707,7 @@ mmas_status mmas_prior_apply_weighted(mmas_prior *p, mmas_handle *h, float gamma
     if (st != MMAS_OK) return st;
     if ((st = forward(p, h)) != MMAS_OK) return st;
     cudaStream_t s = h->stream;
-    PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, s));
+    PCK(p, launch_eta_beta(h->dist, h->n, h->ld, (double)h->p.beta, h->eb, h->ebt, h->maxd_val, s));
     k_prior_weight<<<std::min(h->n, 4096), 256, 0, s>>>(p->s, p->nn, h->n, h->ld, gamma, h->eb);
     PCK(p, cudaGetLastError());
     UpdateArgs refresh = h->uargs;

@@ -74,7 +74,7 @@ void free_all(mmas_handle *h)
                     h->cand32,  h->cand16, h->tours,   h->lens,    h->gb_tour, h->nn_tour,
                     h->nbr,     h->sc,     h->maxd,    h->ext_tour, h->ext_len, h->ext_bad, h->nnd,
                     h->xl32,    h->xlw,    h->xlb,     h->xxw,     h->xxn,  h->xhot,
-                    h->xf16,    h->xfb,    h->far};
+                    h->xf16,    h->xfb,    h->far,     h->ebt};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (h->h_sc) cudaFreeHost(h->h_sc);
@@ -285,7 +285,9 @@ mmas_status create_impl(mmas_handle *h, const mmas_instance *inst)
     *h->h_sc = init;
     CK(h, cudaMemcpyAsync(h->sc, h->h_sc, sizeof(Scalars), cudaMemcpyHostToDevice, s));
 
-    CK(h, launch_eta_beta(h->dist, n, ld, (double)h->p.beta, h->eb, s));
+    h->maxd_val = maxd;
+    if (maxd <= ETA_TABLE_MAX) CK(h, dalloc(&h->ebt, ((size_t)maxd + 1) * sizeof(float), h->stream));
+    CK(h, launch_eta_beta(h->dist, n, ld, (double)h->p.beta, h->eb, h->ebt, h->maxd_val, s));
     CK(h, launch_candidates(h->dist, n, ld, cl, h->cand32, h->cand16, s));
     // greedy fallback (fallback 0): a reach list of the min(REACH_MAX, n - 1)
     // nearest nodes per row, refreshed with choice_info, usually decides it
