@@ -43,7 +43,8 @@ def _ulps(a, b):
 # ------------------------------------------------------------------ set-up
 
 @pytest.mark.parametrize("n,cl,src", [(3, 1, "xy"), (5, 2, "xy"), (33, 8, "xy"), (200, 0, "xy"),
-                                      (300, 12, "dist"), (1000, 32, "xy"), (1500, 16, "xy")])
+                                      (300, 12, "dist"), (1000, 32, "xy"), (1500, 16, "xy"),
+                                      (2000, 64, "xy")])
 def test_setup_matches_oracle(n, cl, src):
     xy = I.uniform(n, 100 + n)
     kw = dict(m=8, cl=cl, rho=0.02, seed=1)
@@ -59,6 +60,22 @@ def test_setup_matches_oracle(n, cl, src):
     tau, tmin, tmax = g.pheromone()
     assert (tmin, tmax) == tuple(o.limits())
     assert np.array_equal(tau, st["tau"])
+    g.close()
+
+
+def test_setup_on_a_lattice_matches_oracle():
+    """A 40 x 25 lattice: every distance repeats many times, so the sorted
+    candidate lists (the K-th smallest distance by bisection, ties taken by
+    id, then sorted) and the nearest-neighbour tour (the first unvisited entry
+    of the row's reach list, ties by id) are decided by the tie rule at almost
+    every step."""
+    xy = I.grid(40, 25, spacing=10)
+    g, o = _pair(xy=xy, m=8, cl=64, rho=0.02, seed=1)
+    s, st = g.setup(), o.state()
+    assert np.array_equal(s["cand"], st["cand"])
+    assert s["nn_len"] == o.nn_len
+    assert _ulps(s["eta_beta"], st["eta_beta"]).max() <= 1
+    assert tuple(g.pheromone()[1:]) == tuple(o.limits())
     g.close()
 
 
