@@ -10,19 +10,19 @@
 // repeat until a run makes no move.
 //
 // Here each round evaluates a window of consecutive cities in parallel, one
-// warp per city (lane h examines neighbour h on both sides, and ballots pick
-// the first improving neighbour in list order), against the current tour, and
-// applies the lowest-index improving move; the window's earlier cities had no
-// move, so they get their bits set.  That is exactly the sequential search,
-// move for move, for any window size: the window is FIRST_WINDOW cities after
-// a move (moves come densely, so a small window wastes few evaluations and
-// leaves the other warps idle) and doubles, up to blockDim, while windows find
-// none.
+// warp per city -- or, with neighbour lists of at most 16, one half-warp per
+// city (lane h examines neighbour h on both sides, and ballots pick the first
+// improving neighbour in list order) -- against the current tour, and applies
+// the lowest-index improving move; the window's earlier cities had no move, so
+// they get their bits set.  That is exactly the sequential search, move for
+// move, for any window size: the window is one city a searching group (at most
+// 16) after a move (moves come densely, so a small window wastes few
+// evaluations) and doubles, up to blockDim, while windows find none.
 //
-// Round protocol.  A warp with a move records it in its own slot (city, side,
-// the two positions, the two new edge lengths) and publishes its city by
-// atomic minimum, so the lowest city wins; the winner's slot then describes
-// the whole move.  The minima live in three rotating words: after the round's
+// Round protocol.  A searching group with a move records it in its own slot
+// (city, side, the two positions, the two new edge lengths) and publishes its
+// city by atomic minimum, so the lowest city wins; the winner's slot then
+// describes the whole move.  The minima live in three rotating words: after the round's
 // barrier a word two rounds ahead is reset, which no thread can still be
 // reading, so a round without a move costs one barrier.
 // A move costs one more: warp 0 alone applies it -- bits of the skipped
@@ -35,8 +35,8 @@
 // footprint).  A move rewrites positions pa - 1 .. pb + 1 only (the reversed
 // path [pa..pb] and the two edges that border it).  So a search whose
 // footprint lies outside pa - 2 .. pb + 2 returns the same result on the new
-// tour as on the old one.  The window's first cities (one a warp) keep their
-// footprints; after the search every warp tests its city's footprint against
+// tour as on the old one.  The window's first cities (one a group) keep their
+// footprints; after the search one warp per kept city tests its footprint against
 // the ranges of the moves of the earlier kept cities (computed from their
 // move records, which stay exact for every move that is applied), and warp 0
 // walks on from the round's first move: a city whose footprint misses every
