@@ -322,6 +322,15 @@ mmas_status mmas_probe_draw_rate(int32_t device, float ms, double *draws_per_s);
  * ECUDA. */
 mmas_status mmas_probe_l2_bandwidth(int32_t device, int64_t bytes, double *gbs);
 
+/* Test hook (not part of the method): the accuracy of the log2 the
+ * candidate-list steps take of their draws (the reservoir key log2(r)/w,
+ * Sec. 4.2.2).  Evaluates it on device `device` at every one of the 2^23 draw
+ * values r = ((x >> 9) + 1/2) 2^-23 and writes the largest relative error
+ * against the double-precision log2 to *max_rel, and that of the library's
+ * log2f to *max_rel_library (may be NULL).  Synchronous; allocates and frees a
+ * 16-byte device buffer.  Errors: EINVAL (NULL max_rel), ECUDA. */
+mmas_status mmas_debug_draw_log2_error(int32_t device, double *max_rel, double *max_rel_library);
+
 /* ---- learned edge prior: tensor-core GEMM ---------------------------------
  *
  * BF16 GEMM on the tensor cores (tcgen05, FP32 accumulation in tensor memory),

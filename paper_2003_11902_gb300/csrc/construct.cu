@@ -473,12 +473,12 @@ __device__ __forceinline__ void cand_group(const ConstructArgs &a, const uint16_
         if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
         if (j == 2) {
             philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
-            nl[0] = log2f(unit_open(nx.x));
-            nl[1] = log2f(unit_open(nx.y));
+            nl[0] = draw_log2(unit_open(nx.x));
+            nl[1] = draw_log2(unit_open(nx.y));
         }
         if (j == 3) {
-            nl[2] = log2f(unit_open(nx.z));
-            nl[3] = log2f(unit_open(nx.w));
+            nl[2] = draw_log2(unit_open(nx.z));
+            nl[3] = draw_log2(unit_open(nx.w));
         }
         const int t = 4 * g + j;
         if (CHECK && (t == 0 || t >= a.n)) continue;
@@ -518,12 +518,12 @@ __device__ __forceinline__ void cand_group_spec(const ConstructArgs &a, const ui
         if (j == 1) philox_rounds_rk<4, 8>(nx, a.rk0, a.rk1);
         if (j == 2) {
             philox_rounds_rk<8, 10>(nx, a.rk0, a.rk1);
-            nl[0] = log2f(unit_open(nx.x));
-            nl[1] = log2f(unit_open(nx.y));
+            nl[0] = draw_log2(unit_open(nx.x));
+            nl[1] = draw_log2(unit_open(nx.y));
         }
         if (j == 3) {
-            nl[2] = log2f(unit_open(nx.z));
-            nl[3] = log2f(unit_open(nx.w));
+            nl[2] = draw_log2(unit_open(nx.z));
+            nl[3] = draw_log2(unit_open(nx.w));
         }
         const int idx = CL32 ? cur * 32 + lane : (act ? cur * a.cl + lane : 0);
         uint32_t v;
@@ -669,9 +669,9 @@ __device__ __forceinline__ void build_tour(const ConstructArgs &a, const uint16_
             uint4 r = make_uint4((uint32_t)lane, 0u, (uint32_t)ant, it);
             philox_rounds<0, 10>(r, a.key0, a.key1);
             lg[0] = 0.0f;  // step 0 is the start node
-            lg[1] = log2f(unit_open(r.y));
-            lg[2] = log2f(unit_open(r.z));
-            lg[3] = log2f(unit_open(r.w));
+            lg[1] = draw_log2(unit_open(r.y));
+            lg[2] = draw_log2(unit_open(r.z));
+            lg[3] = draw_log2(unit_open(r.w));
         }
         cand_group<true, TW, PART>(a, cc, cw, tb, trow, lane, ant, it, 0, lg, cur, twin, fbn);
         int g = 1;
@@ -842,8 +842,8 @@ __device__ __forceinline__ void build_tour_long(const ConstructArgs &a, Tabu<TW>
             philox_rounds_rk<0, 10>(r0, a.rk0, a.rk1);
             philox_rounds_rk<0, 10>(r1, a.rk0, a.rk1);
         }
-        const float lg0 = log2f(unit_open(pick_word(r0, t & 3)));
-        const float lg1 = log2f(unit_open(pick_word(r1, t & 3)));
+        const float lg0 = draw_log2(unit_open(pick_word(r0, t & 3)));
+        const float lg1 = draw_log2(unit_open(pick_word(r1, t & 3)));
         const int next = cand_step2<TW>(a, tb, lane, cur, lg0, lg1, t, ant, it, fbn);
         tb.mark(lane, next);
         twin = (lane == (t & 31)) ? next : twin;

@@ -95,6 +95,35 @@ __device__ __forceinline__ float unit_open(uint32_t x)
     return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.99999994039535522461f);
 }
 
+// log2 of a candidate draw r = ((x >> 9) + 1/2) 2^-23 in (0, 1), to within
+// DRAW_LOG2_MAX_REL relative on that grid of 2^23 values (every one of them is
+// checked by mmas_debug_draw_log2_error).  Below r = 0.55 the hardware's
+// approximate log2, whose error there is at most 2^-22.6 absolute on [0.5, 2)
+// and 2 ulp below 0.5, so about 2.4e-7 relative at most (|log2 r| > 0.86).
+// From 0.55 up, where log2 r nears 0 and an absolute bound is useless:
+// log2(1 + f) with f = r - 1 (exact by Sterbenz) from the series
+// ln((1 + s) / (1 - s)) = 2 (s + s^3/3 + s^5/5 + ...), s = f / (2 + f)
+// (Abramowitz and Stegun 4.1.28), |s| < 0.291: six terms leave a truncation
+// below 3e-8 relative, the fast division 2 ulp.  Measured over every value:
+// 2.55e-7 at most (the library's log2f: 1.07e-7).  The reservoir keys only
+// need their order, so this relative accuracy is what the selection depends on.
+constexpr double DRAW_LOG2_MAX_REL = 2.6e-7;
+__device__ __forceinline__ float draw_log2(float r)
+{
+    const float f = __fsub_rn(r, 1.0f);
+    const float s = __fdividef(f, __fadd_rn(2.0f, f));
+    const float s2 = __fmul_rn(s, s);
+    // (2 / ln 2) / (2i + 1), i = 5 .. 0
+    float p = __fmaf_rn(s2, 0.26230819f, 0.32059890f);
+    p = __fmaf_rn(p, s2, 0.41219858f);
+    p = __fmaf_rn(p, s2, 0.57707802f);
+    p = __fmaf_rn(p, s2, 0.96179669f);
+    p = __fmaf_rn(p, s2, 2.88539008f);
+    const float near1 = __fmul_rn(s, p);
+    const float far = __log2f(r);
+    return r < 0.55f ? far : near1;
+}
+
 // Order-preserving map of a negative float to uint32 (larger float -> larger
 // code), for the reservoir keys log2(r) / w, which are negative (r < 1, w > 0);
 // the codes are >= 1, so 0 still marks "no candidate".

@@ -3,12 +3,13 @@
 // both declared in include/mmas.h.
 //
 // A candidate-list step costs, per candidate slot, one Philox4x32-10 output
-// word (a call yields four), the (0,1) uniform, an accurate log2, the key
+// word (a call yields four), the (0,1) uniform, its log2 (draw_log2), the key
 // multiply by the reciprocal weight and a running maximum of the ordered key
 // (Alg. 4 with log keys, Sec. 4.2.2).  This kernel runs exactly that work and
 // nothing else -- no table loads, no tabu, no reductions -- at full occupancy,
 // so its draw rate is the ALU ceiling the construction is measured against.
 #include <algorithm>
+#include <cstring>
 #include <string>
 
 #include "internal.cuh"
@@ -28,7 +29,7 @@ __global__ void __launch_bounds__(256) k_draw_probe(ConstructArgs a, int iters, 
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const uint32_t k = ord_key(__fmul_rn(log2f(unit_open(w[e])), wi));
+            const uint32_t k = ord_key(__fmul_rn(draw_log2(unit_open(w[e])), wi));
             best = k > best ? k : best;
         }
     }
@@ -54,10 +55,57 @@ __global__ void __launch_bounds__(256) k_l2_probe(const uint4 *__restrict__ buf,
     out[g] = acc;
 }
 
+// Every draw value r = ((x >> 9) + 1/2) 2^-23 (x = k << 9, k = 0 .. 2^23 - 1):
+// the largest relative error of draw_log2 and of the library's log2f against
+// the double-precision log2.
+__global__ void __launch_bounds__(256) k_draw_log2_error(unsigned long long *out)
+{
+    double e_draw = 0.0, e_lib = 0.0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < (1u << 23); k += gridDim.x * blockDim.x) {
+        const float r = unit_open(k << 9);
+        const double t = log2((double)r);  // r < 1: t < 0
+        e_draw = fmax(e_draw, fabs((double)draw_log2(r) - t) / -t);
+        e_lib = fmax(e_lib, fabs((double)log2f(r) - t) / -t);
+    }
+    // non-negative doubles: their bits order like their values
+    atomicMax(out, (unsigned long long)__double_as_longlong(e_draw));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(e_lib));
+}
+
 }  // namespace
 }  // namespace mmas
 
 using namespace mmas;
+
+extern "C" mmas_status mmas_debug_draw_log2_error(int32_t device, double *max_rel, double *max_rel_library)
+{
+    if (!max_rel) {
+        set_thread_error("mmas_debug_draw_log2_error: max_rel must be non-NULL");
+        return MMAS_EINVAL;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    unsigned long long *out = nullptr, h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemset(out, 0, sizeof(h));
+    if (e == cudaSuccess) {
+        k_draw_log2_error<<<1024, 256>>>(out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h, out, sizeof(h), cudaMemcpyDeviceToHost);
+    if (out) cudaFree(out);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("mmas_debug_draw_log2_error: ") + cudaGetErrorString(e));
+        return MMAS_ECUDA;
+    }
+    double v[2];
+    memcpy(v, h, sizeof(v));
+    *max_rel = v[0];
+    if (max_rel_library) *max_rel_library = v[1];
+    return MMAS_OK;
+}
 
 extern "C" mmas_status mmas_probe_l2_bandwidth(int32_t device, int64_t bytes, double *gbs)
 {

@@ -31,7 +31,7 @@ EXPORTS = ["mmas_default_params", "mmas_create", "mmas_iterate", "mmas_best_tour
            "mmas_debug_fail_allocation", "mmas_debug_expire_stage_waits", "mmas_debug_two_opt_move_cap",
            "mmas_shard_best_key", "mmas_shard_tour", "mmas_update_device", "mmas_two_opt_tour",
            "mmas_phase_times", "mmas_score_tours_noalloc", "mmas_probe_draw_rate", "mmas_gemm_bf16",
-           "mmas_probe_l2_bandwidth", "mmas_gemm_bf16_acc",
+           "mmas_probe_l2_bandwidth", "mmas_gemm_bf16_acc", "mmas_debug_draw_log2_error",
            "mmas_prior_create", "mmas_prior_set_params", "mmas_prior_get_params",
            "mmas_prior_scores", "mmas_prior_train", "mmas_prior_grad", "mmas_prior_apply",
            "mmas_prior_destroy", "mmas_prior_last_error", "mmas_prior_apply_weighted",
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH):
             "mmas_score_tours_noalloc": (C.c_int, [C.c_void_p, i32, i32, i32, C.c_void_p,
                                                   C.c_void_p, C.c_void_p, C.c_void_p]),
             "mmas_probe_draw_rate": (C.c_int, [i32, f32, P(C.c_double)]),
+            "mmas_debug_draw_log2_error": (C.c_int, [i32, P(C.c_double), P(C.c_double)]),
             "mmas_probe_l2_bandwidth": (C.c_int, [i32, i64, P(C.c_double)]),
             "mmas_gemm_bf16_acc": (C.c_int, [C.c_void_p, i32, C.c_void_p, i32, C.c_void_p, i32, i32, i32, i32,
                                             C.c_void_p]),
@@ -455,6 +456,14 @@ def mmas_probe_draw_rate(device: int = 0, ms: float = 50.0) -> float:
     v = C.c_double()
     _check(None, load().mmas_probe_draw_rate(device, ms, C.byref(v)))
     return v.value
+
+
+def mmas_debug_draw_log2_error(device: int = 0):
+    """(largest relative error of the draws' log2, that of the library's log2f)
+    over every draw value (a test hook; see include/mmas.h)."""
+    a, b = C.c_double(), C.c_double()
+    _check(None, load().mmas_debug_draw_log2_error(device, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def mmas_probe_l2_bandwidth(device: int = 0, nbytes: int = 32 << 20) -> float:

@@ -688,3 +688,18 @@ def test_lattice_closed_form_bounds_every_gpu_tour():
     assert O.tour_length(O.distances(xy), tour) == best
     assert n * 100 <= best <= 1.02 * n * 100, best
     g.close()
+
+
+def test_draw_log2_is_accurate_on_every_draw_value():
+    """The candidate-list steps take the log2 of their draws with draw_log2
+    (the hardware's approximate log2 below 0.55, a series for log1p above);
+    on every one of the 2^23 draw values its relative error against the
+    double-precision log2 stays within 2.6e-7, so with the key multiply's
+    rounding (2^-24) two keys can change order only when they lie within
+    6.4e-7 of each other, inside the 1e-6 near-tie rule the construction
+    tests allow.  The library's accurate log2f, measured alike, bounds what
+    the comparison can resolve."""
+    err, err_lib = mmas.mmas_debug_draw_log2_error(0)
+    print(f"draw_log2 max relative error {err:.3e} (library log2f {err_lib:.3e})")
+    assert 0.0 < err <= 2.6e-7
+    assert 0.0 < err_lib < 2e-7
